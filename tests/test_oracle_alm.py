@@ -1,0 +1,180 @@
+"""Pins of the oracle's actuator line against geometry and blade-element theory.
+
+Kinematics against the circle the blades trace; element forces in a frozen
+uniform field against the textbook blade-element split into thrust
+(C_L cos phi + C_D sin phi) and driving force (C_L sin phi - C_D cos phi);
+trilinear sampling against hat-function interpolation of brute-force pulled
+moments; Gaussian spreading against the force-sum identity and the continuous
+Gaussian's unit mass; polar lookup against its nodes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2402_13171_gb300 import inputs as I
+
+C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
+
+
+def make_turbine(**kw):
+    t = I.single_turbine(64, 48, 48, diameter=16.0, hub=(20.0, 24.0, 24.0), elements_per_blade=8, **kw)
+    return O.TurbineSpec(**t), t
+
+
+def test_kinematics_circle():
+    T, t = make_turbine()
+    R, ne = t["radius"], t["n_elements"]
+    hub = np.array(t["hub"])
+    for step in (0, 7, 123):
+        for b in range(3):
+            for k in (0, 3, 7):
+                e = O.element_kinematics(T, step, b, k)
+                r = (k + 0.5) * R / ne
+                assert e["r"] == pytest.approx(r)
+                rel = e["pos"] - hub
+                assert np.linalg.norm(rel) == pytest.approx(r, rel=1e-14)
+                assert rel[0] == pytest.approx(0.0, abs=1e-14)  # rotor plane x = hub_x (no yaw)
+                theta = t["omega"] * step + 2 * math.pi * b / 3
+                np.testing.assert_allclose(rel, r * np.array([0, math.cos(theta), math.sin(theta)]), atol=1e-13)
+                # rigid rotation about +x
+                np.testing.assert_allclose(e["vel"], t["omega"] * np.cross([1, 0, 0], rel), atol=1e-15)
+                np.testing.assert_allclose(e["e_t"], np.cross(e["e_axis"], e["e_r"]), atol=1e-15)
+
+
+def test_kinematics_yaw_turns_axis():
+    T, t = make_turbine(yaw=math.radians(90))
+    e = O.element_kinematics(T, 0, 0, 0)
+    np.testing.assert_allclose(e["e_axis"], [0, 1, 0], atol=1e-15)
+    np.testing.assert_allclose(e["e_r"], [-1, 0, 0], atol=1e-15)
+
+
+def uniform_sim(U, nx=64, ny=48, nz=48, **tk):
+    d = O.make_domain(nx, ny, nz, bc=("periodic",) * 3, u_ref=(U, 0, 0))
+    T, t = make_turbine(**tk)
+    s = O.Sim(d, [T])
+    s.init_fields()
+    return s, T, t
+
+
+def test_frozen_field_blade_element_forces():
+    U = 0.05
+    s, T, t = uniform_sim(U)
+    pos, fb, alpha, loads = s.alm_forces(s.f, s.falm, 0)
+    R, ne, Om = t["radius"], t["n_elements"], t["omega"]
+    l = R / ne
+    thrust = torque = 0.0
+    for k in range(ne):
+        r = (k + 0.5) * l
+        W = math.hypot(U, Om * r)
+        phi = math.atan2(U, Om * r)
+        CL = np.interp(phi, t["alpha"], t["cl"])
+        CD = np.interp(phi, t["alpha"], t["cd"])
+        c = t["chord_root"] + (t["chord_tip"] - t["chord_root"]) * r / R
+        q = 0.5 * W * W * c * l
+        f_axial = q * (CL * math.cos(phi) + CD * math.sin(phi))
+        f_tang = q * (CL * math.sin(phi) - CD * math.cos(phi))
+        assert alpha[k] == pytest.approx(phi, abs=1e-12)
+        # blade 0 at theta = 0: e_r = +y, e_t = +z
+        np.testing.assert_allclose(fb[k], [f_axial, 0.0, f_tang], rtol=1e-10, atol=1e-16)
+        thrust += 3 * f_axial
+        torque += 3 * r * f_tang
+    assert loads[0] == pytest.approx(thrust, rel=1e-10)
+    assert loads[1] == pytest.approx(torque, rel=1e-10)
+    assert loads[0] > 0 and loads[1] > 0   # thrust downstream, driving torque
+
+
+def test_sampling_is_hat_interpolation_of_pulled_moments():
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 8, 7, 6
+    d = O.make_domain(nx, ny, nz, body_force=(1e-4, 0, -2e-4))
+    s = O.Sim(d)
+    rho, u, fneq = I.random_state(nx, ny, nz, seed=5)
+    s.init_fields(rho, u, fneq)
+    falm = rng.uniform(-1e-3, 1e-3, (3, nz, ny, nx))
+    f = s.f
+    # brute force: pulled populations by periodic rolls, then moments per cell
+    pulled = np.stack([np.roll(f[q], shift=(int(C[q, 2]), int(C[q, 1]), int(C[q, 0])), axis=(0, 1, 2))
+                       for q in range(27)])
+    R = pulled.sum(0)
+    Ftot = falm + np.array([1e-4, 0, -2e-4])[:, None, None, None]
+    Uc = (np.einsum("qa,qzyx->azyx", C, pulled) + 0.5 * Ftot) / R
+    for p in ([3.3, 2.7, 4.1], [0.0, 6.5, 5.9], [7.25, 0.5, 0.0]):
+        wsum = 0.0
+        r_ref = 0.0
+        u_ref = np.zeros(3)
+        for z in range(nz + 1):
+            for y in range(ny + 1):
+                for x in range(nx + 1):
+                    w = max(0, 1 - abs(x - p[0])) * max(0, 1 - abs(y - p[1])) * max(0, 1 - abs(z - p[2]))
+                    if w == 0:
+                        continue
+                    wsum += w
+                    r_ref += w * R[z % nz, y % ny, x % nx]
+                    u_ref += w * Uc[:, z % nz, y % ny, x % nx]
+        assert wsum == pytest.approx(1.0)
+        r, uu = s.sample(f, falm, 0, p)
+        assert r == pytest.approx(r_ref, abs=1e-14)
+        np.testing.assert_allclose(uu, u_ref, atol=1e-15)
+
+
+def test_gaussian_axis_mass():
+    """By Poisson summation the untruncated lattice sum of the 1-D Gaussian
+    exp(-s^2/eps^2)/(eps sqrt(pi)) is 1 up to ~exp(-pi^2 eps^2); the sum cut at
+    3 eps is therefore 1 minus the discrete tail beyond 3 eps."""
+    for eps in (1.5, 2.0, 3.0):
+        for p in (0.0, 0.3, 17.77):
+            i = np.arange(math.floor(p) - 60, math.floor(p) + 61)
+            s = i - p
+            tail = np.sum(np.exp(-s[np.abs(s) > 3 * eps] ** 2 / eps ** 2)) / (eps * math.sqrt(math.pi))
+            assert O.gauss_axis_sum(p, eps) == pytest.approx(1.0 - tail, abs=2.5 * math.exp(-math.pi ** 2 * eps ** 2) + 1e-14)
+            assert 1e-6 < tail < 1e-4
+
+
+def test_spread_force_sum_and_support():
+    d = O.make_domain(40, 40, 40)
+    rng = np.random.default_rng(22)
+    pos = rng.uniform(12, 28, (5, 3))
+    fb = rng.uniform(-1, 1, (5, 3))
+    eps = 2.0
+    force = O.spread(d, pos, fb, eps)
+    np.testing.assert_allclose(force.reshape(3, -1).sum(1), -fb.sum(0), atol=1e-13)
+    # single element: zero beyond 3 eps per axis, separable and centred
+    f1 = O.spread(d, pos[:1], fb[:1], eps)
+    nz_idx = np.argwhere(np.abs(f1[0]) > 0)
+    p = pos[0]
+    assert np.all(np.abs(nz_idx[:, ::-1] - p) <= 3 * eps + 1e-12)
+    x0, y0, z0 = np.round(p).astype(int)
+    w = f1[0] / -fb[0, 0]
+    gx = np.exp(-((np.arange(40) - p[0]) ** 2) / eps ** 2)
+    # ratio of weights along x at fixed (y0, z0) follows the 1-D Gaussian
+    assert w[z0, y0, x0 + 1] / w[z0, y0, x0] == pytest.approx(gx[x0 + 1] / gx[x0], rel=1e-12)
+    # spread_at agrees with the scatter
+    for (x, y, z) in [(x0, y0, z0), (x0 + 2, y0 - 3, z0 + 1)]:
+        np.testing.assert_allclose(O.spread_at(pos, fb, eps, x, y, z), force[:, z, y, x], atol=1e-15)
+
+
+def test_polar_lookup():
+    a, cl, cd = I.synthetic_polars()
+    assert O.table_lookup(a, cl, a[1000]) == cl[1000]
+    mid = 0.5 * (a[1800] + a[1801])
+    assert O.table_lookup(a, cl, mid) == pytest.approx(0.5 * (cl[1800] + cl[1801]))
+    assert O.table_lookup(a, cd, 10.0) == cd[-1]
+    assert O.table_lookup(a, cd, -10.0) == cd[0]
+    # within table spacing of the analytic polar on the linear part
+    x = math.radians(5.03)
+    assert O.table_lookup(a, cl, x) == pytest.approx(2 * math.pi * x, abs=1e-12)
+    assert O.table_lookup(a, cd, x) == pytest.approx(0.01 + 0.02 * x * x, abs=0.02 * math.radians(0.1) ** 2)
+
+
+def test_alm_step_momentum_balance():
+    """Over one step the fluid momentum changes by exactly minus the sum of the
+    blade forces (the spread conserves force)."""
+    s, T, t = uniform_sim(0.05)
+    j0 = np.einsum("qa,qzyx->a", C, s.f)
+    s.step(1)
+    j1 = np.einsum("qa,qzyx->a", C, s.f)
+    # rounding of a sum of ~1.5e5 cells with total momentum ~7e3
+    np.testing.assert_allclose(j1 - j0, -s.elem_force.sum(0), atol=1e-10)
+    assert s.loads[0, 0] > 0
