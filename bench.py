@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Throughput of the fused D3Q27 cumulant LBM + actuator-line time step.
+
+Workload: the single-rotor case, 256x128x128 cells, velocity inlet 0.05 lu
+with 1 % seeded white noise, zero-gradient outlet, periodic y/z, one
+three-bladed rotor (D = 32 cells at (64, 64, 64), 40 Gaussian-spread elements
+per blade, eps = 2, TSR 6, synthetic polars), FP32 PDF storage.  A step is one
+launch of the fused stream-collide kernel, which also evaluates the actuator
+line of the next step.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline per GB300 (fused LBM+ALM step) vs plain FP32 at stated accuracy"
+WORKLOAD = "single_turbine_256x128x128"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32")
+    p.add_argument("--collision", choices=["cumulant", "srt_smag"], default="cumulant")
+    p.add_argument("--tile", type=str, default="128x1")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_run(steps_hint, budget_s):
+    """The FP64 oracle on the host cores: full rotor + inflow setup of the
+    workload, stream-collide restricted to a slab of z planes through the rotor
+    (a bounded sample).  Returns (seconds per step, cells per step, threads)."""
+    import oracle as O
+    from paper_2402_13171_gb300 import inputs as I
+
+    dom, turb = I.single_turbine_case()
+    d = O.make_domain(dom["nx"], dom["ny"], dom["nz"], collision=dom["collision"], nu=dom["nu"], bc=dom["bc"],
+                      u_ref=dom["u_ref"], noise_rel=dom["noise_rel"], seed=dom["seed"])
+    s = O.Sim(d, [O.TurbineSpec(**turb)])
+    s.init_fields()
+    planes = 8
+    z0 = 56
+    t = time.perf_counter()
+    s.step_planes(z0, z0 + planes)
+    per_plane = (time.perf_counter() - t) / planes
+    planes = int(max(1, min(64, budget_s / max(1, steps_hint) / per_plane)))
+    return s, z0, planes, dom["nx"] * dom["ny"] * planes, O.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    s, z0, planes, cells, threads = oracle_sample_run(args.steps + args.warmup, 150.0)
+    for _ in range(args.warmup):
+        s.step_planes(z0, z0 + planes)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        s.step_planes(z0, z0 + planes)
+    dt = time.perf_counter() - t
+    value = cells * args.steps / dt / 1e6
+    sample = (f"FP64 C oracle, OpenMP; each step: blade kinematics, sampling, forces and Gaussian spreading of the "
+              f"full rotor, then pull + cumulant collision on z planes [{z0}, {z0 + planes}) of the "
+              f"256x128x128 lattice ({cells} cells)")
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "collision": "cumulant", "sample_cells_per_step": cells},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def accuracy_check():
+    """Scaled-down rotor case (48x32x32, D = 12, 3 x 6 elements), 50 steps:
+    max |u_gpu - u_oracle| (FP32 GPU vs FP64 oracle)."""
+    import numpy as np
+    import oracle as O
+    from paper_2402_13171_gb300 import inputs as I
+    from paper_2402_13171_gb300 import lbm
+
+    dom, turb = I.single_turbine_case(48, 32, 32, diameter=12.0, elements_per_blade=6, seed=11)
+    g = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], nu=dom["nu"], bc=dom["bc"], seed=dom["seed"])
+    g.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
+    g.add_turbine(**turb)
+    g.step(50)
+    _, ug = g.moments()
+    d = O.make_domain(dom["nx"], dom["ny"], dom["nz"], nu=dom["nu"], bc=dom["bc"], u_ref=dom["u_ref"],
+                      noise_rel=dom["noise_rel"], seed=dom["seed"])
+    s = O.Sim(d, [O.TurbineSpec(**turb)])
+    s.init_fields()
+    s.step(50)
+    _, uo = s.moments()
+    g.destroy()
+    return float(np.abs(ug - uo).max())
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2402_13171_gb300 import build as B
+    from paper_2402_13171_gb300 import inputs as I
+    from paper_2402_13171_gb300 import lbm
+
+    rank, world, local = dist_info()
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    tx, ty = (int(v) for v in args.tile.split("x"))
+    dom, turb = I.single_turbine_case()
+    dom["collision"] = args.collision
+    lat = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], device=local, collision=args.collision,
+                             nu=dom["nu"], smag_c=dom["smag_c"], storage=args.storage, bc=dom["bc"],
+                             seed=dom["seed"], tile=(tx, ty))
+    lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
+    lat.add_turbine(**turb)
+    bytes_per_cell, cells = lat.traffic_model()
+    lat.step(args.warmup)
+    lat.sync()
+
+    # ---- timed region: K launches, CUDA events on the launch stream, per-kernel events inside
+    clocks = ClockSampler(local)
+    lat.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(lat.stream)
+    lat.step(args.steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    lat.sync()
+    elapsed_ms = e0.elapsed_time(e1)
+    kernel_ms, launches = lat.kernel_time()
+    lat.set_profiling(False)
+    t_local = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    elapsed_ms, kernel_ms = float(t_local[0]), float(t_local[1])
+    value = world * cells * args.steps / (elapsed_ms * 1e-3) / 1e6
+    peak, peak_kind = load_peaks()
+    achieved = bytes_per_cell * cells / (kernel_ms * 1e-3) / 1e9
+    thrust, torque = lat.loads(0)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        N = cells
+        rho_h = torch.ones(N, dtype=torch.float64).pin_memory().numpy()
+        u_h = torch.zeros(3 * N, dtype=torch.float64).pin_memory().numpy()
+        u_h[:N] = dom["u_ref"][0]
+        barrier()
+        t = time.perf_counter()
+        lat.init_fields(rho_h, u_h)
+        for _ in range(args.steps):
+            lat.step(1)
+            lat.loads(0)
+        rho_o, u_o = lat.moments()
+        barrier()
+        dt = time.perf_counter() - t
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt[0])
+        e2e = {"value": world * cells * args.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 16.0 * N / args.steps,
+               "d2h_bytes_per_step": 16.0 + 32.0 * N / args.steps,
+               "api": "lbm_init_fields(host rho, u) + K x (lbm_step(1) + alm_get_loads) + lbm_get_moments"}
+
+    acc = None
+    cpu = None
+    if rank == 0 and world == 1:
+        acc = accuracy_check()
+        if not args.no_cpu_baseline:
+            s, z0, planes, ccells, threads = oracle_sample_run(30, 20.0)
+            nst = 5
+            t = time.perf_counter()
+            for _ in range(nst):
+                s.step_planes(z0, z0 + planes)
+            dt = time.perf_counter() - t
+            cpu = {"value": ccells * nst / dt / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": f"FP64 C oracle, {nst} steps of the full rotor + pull/cumulant collision on z planes "
+                             f"[{z0}, {z0 + planes}) of the 256x128x128 lattice ({ccells} cells per step)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "storage": args.storage, "collision": args.collision,
+                       "rotor": "3 blades x 40 elements, D=32 at (64,64,64), eps=2, TSR 6",
+                       "tile": args.tile, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": f"no flush: PDF arrays {2 * bytes_per_cell / 2 * cells / 1e6:.0f} MB > 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_step (fused stream-collide + in-kernel ALM)",
+                         "bytes_per_cell": bytes_per_cell, "kernel_ms": kernel_ms, "peak_kind": peak_kind},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "accuracy": {"max_du_vs_fp64_oracle": acc, "case": "48x32x32 rotor, 50 steps"} if acc is not None else None,
+            "loads": {"thrust": thrust, "torque": torque},
+        }
+        print(json.dumps(line), flush=True)
+    lat.destroy()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * lbm_gb300.h -- C ABI of the GB300 (sm_103a) D3Q27 lattice-Boltzmann solver
+ * coupled to the actuator line model, the method of arxiv 2402.13171.
+ *
+ * One time step (Sec. 2.1 and 2.2 of the paper, in this order):
+ *   1. blade kinematics at t = n (Algorithm 2, Line::update);
+ *   2. trilinear sampling of rho and u at every blade element (Sec. 2.2);
+ *   3. blade-element forces from tabulated polars (Sec. 2.2, element-force equation);
+ *   4. regularisation of the element forces onto the lattice, f_eps = f (x) eta_eps (Sec. 2.2),
+ *      with a Gaussian kernel;
+ *   5. pull streaming with boundary rules, and
+ *   6. cumulant collision (Geier et al. 2015, Sec. 2.1) or BGK-Smagorinsky with Guo forcing
+ *      (Sec. 2.1, lattice Boltzmann equation with source term).
+ * Steps 5-6 run fused in one kernel over the lattice; steps 1-4 of step n+1
+ * run inside the kernel of step n as soon as the cells around the rotor are
+ * written, so a time step is a single kernel launch.
+ *
+ * Conventions shared by every call:
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, relaxation rate omega = 1/(3 nu + 1/2).
+ *  - Velocities q = (cz+1)*9 + (cy+1)*3 + (cx+1), cx, cy, cz in {-1, 0, 1};
+ *    q = 13 is the rest population, opposite(q) = 26 - q.
+ *  - Host field arrays are x fastest: scalar fields [nz][ny][nx], vector fields
+ *    3 planes [3][nz][ny][nx], PDF fields 27 planes [27][nz][ny][nx].
+ *  - Device PDFs are stored as offsets f_q - w_q from the lattice weights, in
+ *    FP32, BF16 or FP16 (lbm_config.storage); collision arithmetic is FP32.
+ *  - Every function returns an lbm_status.  The first error is sticky: every
+ *    later call on the same context returns it until lbm_destroy.  No C++
+ *    exception crosses this interface.  lbm_last_error() gives the message.
+ *  - The context owns all device memory it allocates (through
+ *    lbm_config.dev_alloc/dev_free if given, else cudaMalloc/cudaFree).  The
+ *    caller owns every host array it passes; tables are copied.
+ *  - Calls that return host data synchronise the context's stream; lbm_step
+ *    only enqueues work.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque handle of one lattice (one instance) */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* bad pointer, size or value; the context stays usable */
+    LBM_ERR_OOM = 2,         /* device allocation failed */
+    LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    LBM_ERR_NUMERIC = 4,     /* NaN/Inf seen by the diagnostic sums */
+    LBM_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    LBM_ERR_STATE = 6,       /* call not valid in the current state */
+    LBM_ERR_UNSUPPORTED = 7  /* combination not built */
+} lbm_status;
+
+typedef enum { LBM_COLL_CUMULANT = 0, LBM_COLL_SRT_SMAGORINSKY = 1 } lbm_collision;
+typedef enum { LBM_STORE_FP32 = 0, LBM_STORE_BF16 = 1, LBM_STORE_FP16 = 2 } lbm_storage;
+typedef enum {
+    LBM_BC_PERIODIC = 0,       /* source index wraps */
+    LBM_BC_INFLOW_OUTFLOW = 1, /* x only: equilibrium inlet at x = 0 (rho = 1, lbm_inflow velocity),
+                                  zero-gradient outlet at x = nx-1 */
+    LBM_BC_NOSLIP = 2          /* halfway bounce-back walls at -1/2 and n-1/2 */
+} lbm_bc;
+
+typedef struct {
+    int nx, ny, nz;          /* cells; each in [1, 65535] */
+    int collision;           /* lbm_collision */
+    double nu;               /* lattice kinematic viscosity, > 0 */
+    double smag_c;           /* Smagorinsky constant (SRT variant only) */
+    int storage;             /* lbm_storage */
+    int bc[3];               /* lbm_bc per axis */
+    double body_force[3];    /* uniform body force density, added to the ALM force */
+    unsigned long long seed; /* key of the inflow noise (splitmix64) */
+    int diag_every;          /* FP64 mass/momentum sums every k steps (0 = off) */
+    void* cuda_stream;       /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    void* (*dev_alloc)(size_t bytes, void* user); /* optional device allocator */
+    void (*dev_free)(void* ptr, void* user);
+    void* alloc_user;
+    int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 128 x 1 */
+} lbm_config;
+
+typedef struct {
+    int kind;          /* 0: uniform u_ref; 1: log law u_ref * ln(z_c/z0)/ln(z_ref/z0), z_c = z + 1/2 */
+    double u_ref[3];
+    double z0, z_ref;
+    double noise_rel;  /* per component, per step and inlet column: + noise_rel * |u_ref| * xi,
+                          xi uniform in [-1, 1) from splitmix64(seed, ((n*nz + z)*ny + y)*3 + a + 1) */
+} lbm_inflow;
+
+/* One rotor of n_blades straight blade lines (Sec. 2.2; kinematics of
+ * Algorithm 2).  Rotor axis (cos yaw, sin yaw, 0); blade b at angle
+ * theta0 + omega * n + 2 pi b / n_blades about it; element k at radius
+ * (k + 1/2) R / n_elements, length R / n_elements, chord linear from
+ * chord_root (r = 0) to chord_tip (r = R); alpha = phi - twist_k - pitch.
+ * The polar table (alpha ascending, radians) is interpolated linearly and
+ * clamped at its ends.  The whole force support (hub +- (R + 3 eps + 1)) must
+ * lie inside [1, n-2] on every axis, and epsilon must be in [0.5, 5]. */
+typedef struct {
+    double hub[3];
+    double radius;
+    int n_blades, n_elements;
+    double epsilon;       /* Gaussian width, cells */
+    double omega;         /* rotor speed, rad per step, positive about the axis */
+    double yaw, pitch, theta0;
+    double chord_root, chord_tip;
+    const double* twist;  /* n_elements values or NULL (0) */
+    int n_polar;          /* >= 2 */
+    const double* alpha;
+    const double* cl;
+    const double* cd;
+} alm_turbine_desc;
+
+/* Create one lattice.  The state starts at f = feq(rho = 1, u = 0) until
+ * lbm_set_inflow / lbm_init_fields set it; the step counter starts at 0.
+ * Errors: INVALID_ARG (sizes, collision/storage/bc codes, nu <= 0), OOM, CUDA. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out);
+
+/* Create n lattices that step together in one launch per time step (the
+ * batched form of lbm_step).  cfgs[i] may differ in sizes, viscosity, inflow
+ * and rotors, but collision, storage and cuda_stream must agree
+ * (UNSUPPORTED otherwise).  out receives n handles; lbm_step on any of them
+ * advances all n.  Each handle is destroyed with lbm_destroy; memory is freed
+ * with the last one. */
+lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_ctx** out);
+
+/* Inflow of the x inlet (reading: the paper's validation runs are periodic).
+ * Also sets the state to feq(rho = 1, u = mean inflow) everywhere and the
+ * lagged ALM force to zero; the step counter is unchanged. */
+lbm_status lbm_set_inflow(lbm_ctx* ctx, const lbm_inflow* inflow);
+
+/* Set the state to feq(rho, u) + fneq (host arrays: rho [N] or NULL for 1,
+ * u [3][N] or NULL for the mean inflow, fneq [27][N] or NULL for 0) and the
+ * lagged ALM force to zero; the step counter is unchanged.  Synchronises. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, const float* fneq);
+
+/* Add a rotor (copied).  id_out receives its index within this lattice.
+ * Errors: INVALID_ARG for a support outside [1, n-2], bad epsilon, table or
+ * element counts (at most 4096 elements per lattice). */
+lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* desc, int* id_out);
+
+/* Enqueue n_steps time steps on the stream (replays of a captured CUDA graph
+ * when profiling is off).  Errors from earlier steps surface here or at the
+ * next synchronising call. */
+lbm_status lbm_step(lbm_ctx* ctx, int n_steps);
+
+/* Wait for the stream; report any device-side error. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* rho [N] and u [3][N] of the last collision: rho = sum f*, u = (sum c f* -
+ * F/2)/rho with F the force of that collision (the velocity the collision
+ * used).  Host arrays, caller-owned.  Synchronises. */
+lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u);
+
+/* Absolute populations f [27][N] (host, FP64) / overwrite them (checkpoint
+ * restore: the step counter and lagged ALM force are kept).  Synchronises. */
+lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f);
+lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f);
+
+/* Rotor thrust and torque (FP64 sums, Sec. 2.2) of the forces applied in the
+ * last completed step; optionally the element blade forces and positions
+ * (3 floats each, blade-major).  Synchronises. */
+lbm_status alm_get_loads(lbm_ctx* ctx, int id, double* thrust, double* torque, float* elem_force, float* elem_pos);
+
+/* FP64 sums [mass, momentum x, y, z] of the last diagnostic step (post-
+ * collision state).  Synchronises; NUMERIC if NaN/Inf was seen. */
+lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_step);
+
+/* Completed-step counter n (also the key of the inflow noise and blade angle),
+ * shared by all lattices of a batch.  lbm_set_step sets it (checkpoint
+ * restore together with lbm_set_pdfs) and re-evaluates the actuator line for
+ * step n.  Synchronises. */
+lbm_status lbm_get_step(lbm_ctx* ctx, long long* step);
+lbm_status lbm_set_step(lbm_ctx* ctx, long long step);
+
+/* Kernel timing: when enabled, lbm_step launches kernels one by one with CUDA
+ * events around every stream-collide launch; lbm_get_kernel_time returns the
+ * mean duration (ms) and the number of timed launches since enabling. */
+lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable);
+lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches);
+
+/* Algorithmic bytes one stream-collide launch moves per cell (27 loads + 27
+ * stores of the storage type) and the number of cells of one launch. */
+lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_launch);
+
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_status_string(lbm_status s);
+
+/* Free the handle (and the batch's device memory with its last handle). NULL-safe. */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

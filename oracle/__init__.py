@@ -36,13 +36,19 @@ NQ = 27
 
 def build(force: bool = False) -> str:
     """Compile the C oracle into a shared library (gcc, OpenMP, -O2, no fast-math)."""
+    import platform
     os.makedirs(_BUILD, exist_ok=True)
+    stamp = os.path.join(_BUILD, "ARCH")
+    if (open(stamp).read().strip() if os.path.exists(stamp) else "") != platform.machine():
+        force = True
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
+    with open(stamp, "w") as f:
+        f.write(platform.machine())
     return _LIB
 
 
@@ -123,6 +129,8 @@ def _declare(L):
     L.or_spread_at.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
     L.or_step.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), ctypes.c_int, _dp, _dp, _dp, _dp, c_long,
                           _dp, _dp, _dp]
+    L.or_step_planes.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), ctypes.c_int, _dp, _dp, _dp, _dp,
+                                 c_long, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
     L.or_update_cell.argtypes = [ctypes.POINTER(Domain), _dp, _dp, c_long, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
     L.or_moments.argtypes = [ctypes.POINTER(Domain), _dp, _dp, _dp, _dp]
     L.or_init_fields.argtypes = [ctypes.POINTER(Domain), _dp, _dp, _fp, _dp]
@@ -342,6 +350,16 @@ class Sim:
             self.f, self.g = self.g, self.f
             self.falm, self.falm_next = self.falm_next, self.falm
             self.step_count += 1
+
+    def step_planes(self, z_begin, z_end):
+        """One step whose stream-collide part covers planes [z_begin, z_end) only
+        (a bounded CPU-timing sample; the state outside is not advanced)."""
+        lib().or_step_planes(ctypes.byref(self.dom), self._tarr, len(self.turbines), _p(self.f), _p(self.g),
+                             _p(self.falm), _p(self.falm_next), self.step_count, _p(self.loads), _p(self.elem_pos),
+                             _p(self.elem_force), int(z_begin), int(z_end))
+        self.f, self.g = self.g, self.f
+        self.falm, self.falm_next = self.falm_next, self.falm
+        self.step_count += 1
 
     def moments(self):
         rho = np.zeros((self.dom.nz, self.dom.ny, self.dom.nx))

@@ -823,10 +823,12 @@ void or_spread_at(const double* pos, const double* fblade, int n_el, double eps,
  *  7. store into fdst.
  * falm_prev: ALM force field of the previous step (NULL = zero).  loads:
  * 2 doubles per turbine.  elem_pos / elem_force: 3 doubles per element,
- * turbines in order (may be NULL).
+ * turbines in order (may be NULL).  Steps 5-7 run on planes z_begin .. z_end-1
+ * only (a bounded sample for CPU timing); or_step runs all planes.
  */
-void or_step(const or_domain* d, const or_turbine* turbs, int n_turb, const double* fsrc, double* fdst,
-             const double* falm_prev, double* falm_out, long step, double* loads, double* elem_pos, double* elem_force)
+void or_step_planes(const or_domain* d, const or_turbine* turbs, int n_turb, const double* fsrc, double* fdst,
+                    const double* falm_prev, double* falm_out, long step, double* loads, double* elem_pos,
+                    double* elem_force, int z_begin, int z_end)
 {
     build_partition_terms();
     size_t N = (size_t)d->nx * d->ny * d->nz;
@@ -846,7 +848,7 @@ void or_step(const or_domain* d, const or_turbine* turbs, int n_turb, const doub
         free(fb);
     }
 #pragma omp parallel for schedule(static)
-    for (int z = 0; z < d->nz; ++z) {
+    for (int z = z_begin; z < z_end; ++z) {
         for (int y = 0; y < d->ny; ++y) {
             for (int x = 0; x < d->nx; ++x) {
                 double f[NQ], fo[NQ], F[3];
@@ -858,6 +860,13 @@ void or_step(const or_domain* d, const or_turbine* turbs, int n_turb, const doub
             }
         }
     }
+}
+
+/* The whole lattice (planes 0 .. nz-1). */
+void or_step(const or_domain* d, const or_turbine* turbs, int n_turb, const double* fsrc, double* fdst,
+             const double* falm_prev, double* falm_out, long step, double* loads, double* elem_pos, double* elem_force)
+{
+    or_step_planes(d, turbs, n_turb, fsrc, fdst, falm_prev, falm_out, step, loads, elem_pos, elem_force, 0, d->nz);
 }
 
 /* Post-collision update of a single cell (pull + collide) for sampled checks. */

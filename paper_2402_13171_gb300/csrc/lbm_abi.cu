@@ -1,0 +1,819 @@
+// Host runtime behind the C ABI of include/lbm_gb300.h: lattice contexts and
+// batches, device memory, the per-step work list (rotor tiles first), CUDA
+// graph replay of the single-launch time step, state input/output, and error
+// reporting.  All compute runs in the kernels of lbm_kernels.cu.
+#include "lbm_gb300.h"
+#include "lbm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace lbmgb;
+
+namespace {
+
+struct TurbineHost {
+    alm_turbine_desc desc{};
+    std::vector<double> twist, alpha, cl, cd;
+    DevTurbine dev{};
+};
+
+struct Instance {
+    lbm_config cfg{};
+    DevDomain h{};
+    std::vector<TurbineHost> turb;
+    DevTurbine* d_turb = nullptr;
+    unsigned char* small = nullptr;  // counters, diagnostics, error flags
+};
+
+struct Batch {
+    int refs = 0;
+    std::vector<Instance> inst;
+    int coll = 0, store = 0;
+    cudaStream_t stream = nullptr;
+    void* (*ualloc)(size_t, void*) = nullptr;
+    void (*ufree)(void*, void*) = nullptr;
+    void* user = nullptr;
+    std::vector<void*> allocs;
+    DevDomain* d_dom = nullptr;
+    unsigned long long* d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    unsigned n_tiles = 0;
+    long long* d_step = nullptr;          // two slots: step n lives in slot [n & 1]
+    unsigned int* d_diag_done = nullptr;
+    int diag_every = 0;
+    long long host_step = 0;
+    int tile_x = 128, tile_y = 1;
+    lbm_status status = LBM_OK;
+    std::string err;
+    bool dirty = true;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double prof_ms = 0.0;
+    long long prof_n = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    Batch* b;
+    int idx;
+};
+
+namespace {
+
+size_t store_bytes(int s) { return s == STORE_FP32 ? 4 : 2; }
+
+double w1h(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+double wqh(int q) { return w1h(q % 3 - 1) * w1h((q / 3) % 3 - 1) * w1h(q / 9 - 1); }
+
+lbm_status fail(Batch* b, lbm_status s, const std::string& msg, bool sticky = true)
+{
+    b->err = msg;
+    if (sticky && b->status == LBM_OK) b->status = s;
+    return s;
+}
+
+#define CK(x)                                                                                         \
+    do {                                                                                              \
+        cudaError_t e_ = (x);                                                                         \
+        if (e_ != cudaSuccess) return fail(b, LBM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void* dalloc(Batch* b, size_t bytes)
+{
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (b->ualloc) {
+        p = b->ualloc(bytes, b->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) b->allocs.push_back(p);
+    return p;
+}
+
+void dfree(Batch* b, void* p)
+{
+    if (!p) return;
+    auto it = std::find(b->allocs.begin(), b->allocs.end(), p);
+    if (it != b->allocs.end()) b->allocs.erase(it);
+    if (b->ufree) b->ufree(p, b->user);
+    else cudaFree(p);
+}
+
+void drop_graphs(Batch* b)
+{
+    for (auto& g : b->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+void destroy_batch(Batch* b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    drop_graphs(b);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    std::vector<void*> all = b->allocs;
+    for (void* p : all) dfree(b, p);
+    delete b;
+}
+
+lbm_status validate_cfg(const lbm_config* c, std::string& msg)
+{
+    if (!c) { msg = "null config"; return LBM_ERR_INVALID_ARG; }
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1 || c->nx > 65535 || c->ny > 65535 || c->nz > 65535) {
+        msg = "lattice sizes must be in [1, 65535]";
+        return LBM_ERR_INVALID_ARG;
+    }
+    if ((long long)c->nx * c->ny * c->nz * 27LL >= (1LL << 40)) { msg = "lattice too large"; return LBM_ERR_INVALID_ARG; }
+    if (c->collision != LBM_COLL_CUMULANT && c->collision != LBM_COLL_SRT_SMAGORINSKY) {
+        msg = "unknown collision";
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (c->storage < 0 || c->storage > 2) { msg = "unknown storage"; return LBM_ERR_INVALID_ARG; }
+    if (!(c->nu > 0.0) || !std::isfinite(c->nu)) { msg = "nu must be > 0"; return LBM_ERR_INVALID_ARG; }
+    for (int a = 0; a < 3; ++a) {
+        if (c->bc[a] < 0 || c->bc[a] > 2) { msg = "unknown boundary code"; return LBM_ERR_INVALID_ARG; }
+        if (a > 0 && c->bc[a] == LBM_BC_INFLOW_OUTFLOW) { msg = "inflow/outflow is x only"; return LBM_ERR_INVALID_ARG; }
+    }
+    if (c->bc[0] == LBM_BC_INFLOW_OUTFLOW && c->nx < 2) { msg = "inflow/outflow needs nx >= 2"; return LBM_ERR_INVALID_ARG; }
+    if (c->diag_every < 0) { msg = "diag_every must be >= 0"; return LBM_ERR_INVALID_ARG; }
+    const int tx = c->tile_x ? c->tile_x : 128, ty = c->tile_y ? c->tile_y : 1;
+    if (tx < 32 || tx % 32 != 0 || ty < 1 || tx * ty > 256) {
+        msg = "tile_x must be a multiple of 32 and tile_x * tile_y <= 256";
+        return LBM_ERR_INVALID_ARG;
+    }
+    return LBM_OK;
+}
+
+lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
+{
+    I.cfg = c;
+    DevDomain& h = I.h;
+    h.nx = c.nx;
+    h.ny = c.ny;
+    h.nz = c.nz;
+    h.N = (long long)c.nx * c.ny * c.nz;
+    for (int a = 0; a < 3; ++a) {
+        h.bc[a] = c.bc[a];
+        h.body[a] = (float)c.body_force[a];
+        h.u_ref[a] = 0.0;
+    }
+    h.tau0 = (float)(3.0 * c.nu + 0.5);
+    h.omega = (float)(1.0 / (3.0 * c.nu + 0.5));
+    h.smag_c2 = (float)(c.smag_c * c.smag_c);
+    h.inflow_kind = 0;
+    h.z0 = 0.1;
+    h.inv_log_zref_z0 = 1.0;
+    h.noise_amp = 0.0;
+    h.seed = c.seed;
+    const size_t fbytes = (size_t)h.N * 27 * store_bytes(b->store);
+    for (int p = 0; p < 2; ++p) {
+        h.f[p] = dalloc(b, fbytes);
+        if (!h.f[p]) return fail(b, LBM_ERR_OOM, "PDF array allocation failed");
+        CK(cudaMemsetAsync(h.f[p], 0, fbytes, b->stream));  // offsets 0: f = w, the rest state
+    }
+    I.d_turb = (DevTurbine*)dalloc(b, sizeof(DevTurbine) * kMaxTurbines);
+    void* ep = dalloc(b, sizeof(float4) * kMaxElements * 4);
+    void* el = dalloc(b, sizeof(double) * 2 * kMaxElements);
+    void* ec = dalloc(b, sizeof(float4) * 8 * kMaxElements);
+    void* ld = dalloc(b, sizeof(double) * 4 * kMaxTurbines);
+    I.small = (unsigned char*)dalloc(b, 256);
+    if (!I.d_turb || !ep || !el || !ec || !ld || !I.small) return fail(b, LBM_ERR_OOM, "descriptor allocation failed");
+    CK(cudaMemsetAsync(ep, 0, sizeof(float4) * kMaxElements * 4, b->stream));
+    CK(cudaMemsetAsync(el, 0, sizeof(double) * 2 * kMaxElements, b->stream));
+    CK(cudaMemsetAsync(ld, 0, sizeof(double) * 4 * kMaxTurbines, b->stream));
+    CK(cudaMemsetAsync(I.small, 0, 256, b->stream));
+    float4* e4 = (float4*)ep;
+    h.el_pos[0] = e4;
+    h.el_pos[1] = e4 + kMaxElements;
+    h.el_force[0] = e4 + 2 * kMaxElements;
+    h.el_force[1] = e4 + 3 * kMaxElements;
+    h.el_load = (double*)el;
+    h.el_corner = (float4*)ec;
+    h.loads[0] = (double*)ld;
+    h.loads[1] = (double*)ld + 2 * kMaxTurbines;
+    h.diag_acc = (double*)I.small;             // 4 doubles
+    h.diag_res = (double*)I.small + 4;         // 5 doubles
+    h.rotor_counter = (unsigned int*)(I.small + 128);
+    h.err = (unsigned int*)(I.small + 132);
+    h.turb = I.d_turb;
+    h.n_turb = 0;
+    h.n_el = 0;
+    h.n_rotor_tiles = 0;
+    h.diag_every = c.diag_every;
+    return LBM_OK;
+}
+
+// Upload descriptors and rebuild the work list: rotor tiles of every lattice first.
+lbm_status sync_descriptors(Batch* b)
+{
+    if (!b->dirty) return LBM_OK;
+    std::vector<unsigned long long> rotor, rest;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        Instance& I = b->inst[i];
+        int nrot = 0;
+        for (int z = 0; z < I.h.nz; ++z)
+            for (int y0 = 0; y0 < I.h.ny; y0 += b->tile_y)
+                for (int x0 = 0; x0 < I.h.nx; x0 += b->tile_x) {
+                    bool hit = false;
+                    for (auto& t : I.turb) {
+                        const DevTurbine& B = t.dev;
+                        if (z >= B.lo[2] && z <= B.hi[2] && y0 <= B.hi[1] && y0 + b->tile_y - 1 >= B.lo[1] &&
+                            x0 <= B.hi[0] && x0 + b->tile_x - 1 >= B.lo[0])
+                            hit = true;
+                    }
+                    if (hit) {
+                        rotor.push_back(pack_tile((int)i, z, y0, x0, true));
+                        ++nrot;
+                    } else {
+                        rest.push_back(pack_tile((int)i, z, y0, x0, false));
+                    }
+                }
+        I.h.n_rotor_tiles = nrot;
+        std::vector<DevTurbine> dt;
+        for (auto& t : I.turb) dt.push_back(t.dev);
+        if (!dt.empty())
+            CK(cudaMemcpyAsync(I.d_turb, dt.data(), sizeof(DevTurbine) * dt.size(), cudaMemcpyHostToDevice, b->stream));
+    }
+    std::vector<unsigned long long> tiles = rotor;
+    tiles.insert(tiles.end(), rest.begin(), rest.end());
+    if (tiles.size() > b->tiles_cap) {
+        if (b->d_tiles) dfree(b, b->d_tiles);
+        b->d_tiles = (unsigned long long*)dalloc(b, sizeof(unsigned long long) * tiles.size());
+        if (!b->d_tiles) return fail(b, LBM_ERR_OOM, "work list allocation failed");
+        b->tiles_cap = tiles.size();
+    }
+    b->n_tiles = (unsigned)tiles.size();
+    CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(unsigned long long) * tiles.size(), cudaMemcpyHostToDevice,
+                       b->stream));
+    std::vector<DevDomain> doms;
+    for (auto& I : b->inst) doms.push_back(I.h);
+    CK(cudaMemcpyAsync(b->d_dom, doms.data(), sizeof(DevDomain) * doms.size(), cudaMemcpyHostToDevice, b->stream));
+    // pageable copies above are staged before returning; the stream orders them before any launch
+    drop_graphs(b);
+    b->dirty = false;
+    return LBM_OK;
+}
+
+StepArgs step_args(Batch* b, int parity)
+{
+    StepArgs a;
+    a.dom = b->d_dom;
+    a.tiles = b->d_tiles;
+    a.n_tiles = b->n_tiles;
+    a.n_inst = (int)b->inst.size();
+    a.parity = parity;
+    a.step_slot = b->d_step;
+    a.diag_done = b->d_diag_done;
+    a.diag_every = b->diag_every;
+    return a;
+}
+
+lbm_status launch_one(Batch* b, int parity)
+{
+    const dim3 grid(b->n_tiles), block(b->tile_x, b->tile_y);
+    CK(launch_step(b->coll, b->store, grid, block, b->stream, step_args(b, parity)));
+    return LBM_OK;
+}
+
+// Actuator line of the current step for every lattice (after a state change).
+lbm_status refresh_alm(Batch* b)
+{
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    bool any = false;
+    for (auto& I : b->inst) any = any || I.h.n_el > 0;
+    if (!any) return LBM_OK;
+    CK(launch_alm(b->store, b->d_dom, (int)b->inst.size(), (int)(b->host_step & 1), b->host_step, b->stream));
+    return LBM_OK;
+}
+
+lbm_status zero_fbox(Batch* b, Instance& I)
+{
+    for (auto& t : I.turb) CK(cudaMemsetAsync(t.dev.fbox, 0, sizeof(float) * 3 * t.dev.bcells, b->stream));
+    return LBM_OK;
+}
+
+lbm_status check_device_errors(Batch* b)
+{
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    else CK(cudaDeviceSynchronize());
+    for (auto& I : b->inst) {
+        unsigned e = 0;
+        CK(cudaMemcpy(&e, I.h.err, sizeof e, cudaMemcpyDeviceToHost));
+        if (e & ERR_NONFINITE) return fail(b, LBM_ERR_NUMERIC, "non-finite mass or momentum in the diagnostic sums");
+        if (e & ERR_ELEMENT_OUTSIDE) return fail(b, LBM_ERR_STATE, "a blade element left the lattice interior");
+    }
+    return LBM_OK;
+}
+
+lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
+{
+    if (!out || n < 1 || n > kMaxInstances) return LBM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        std::string msg;
+        if (validate_cfg(cfgs + i, msg) != LBM_OK) return LBM_ERR_INVALID_ARG;
+        if (cfgs[i].collision != cfgs[0].collision || cfgs[i].storage != cfgs[0].storage ||
+            cfgs[i].cuda_stream != cfgs[0].cuda_stream || cfgs[i].tile_x != cfgs[0].tile_x ||
+            cfgs[i].tile_y != cfgs[0].tile_y || cfgs[i].diag_every != cfgs[0].diag_every)
+            return LBM_ERR_UNSUPPORTED;
+    }
+    Batch* b = new Batch();
+    b->coll = cfgs[0].collision;
+    b->store = cfgs[0].storage;
+    b->stream = (cudaStream_t)cfgs[0].cuda_stream;
+    b->ualloc = cfgs[0].dev_alloc;
+    b->ufree = cfgs[0].dev_free;
+    b->user = cfgs[0].alloc_user;
+    b->tile_x = cfgs[0].tile_x ? cfgs[0].tile_x : 128;
+    b->tile_y = cfgs[0].tile_y ? cfgs[0].tile_y : 1;
+    b->diag_every = cfgs[0].diag_every;
+    b->inst.resize(n);
+    lbm_status s = LBM_OK;
+    for (int i = 0; i < n && s == LBM_OK; ++i) s = init_instance(b, b->inst[i], cfgs[i]);
+    if (s == LBM_OK) {
+        b->d_dom = (DevDomain*)dalloc(b, sizeof(DevDomain) * n);
+        void* sc = dalloc(b, 64);
+        if (!b->d_dom || !sc) s = LBM_ERR_OOM;
+        else {
+            b->d_step = (long long*)sc;
+            b->d_diag_done = (unsigned int*)((char*)sc + 16);
+            if (cudaMemsetAsync(sc, 0, 64, b->stream) != cudaSuccess) s = LBM_ERR_CUDA;
+        }
+    }
+    if (s == LBM_OK) s = sync_descriptors(b);
+    if (s == LBM_OK && b->stream) s = cudaStreamSynchronize(b->stream) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    if (s != LBM_OK) {
+        destroy_batch(b);
+        return s;
+    }
+    for (int i = 0; i < n; ++i) {
+        out[i] = new lbm_ctx;
+        out[i]->b = b;
+        out[i]->idx = i;
+        b->refs++;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_NUMERIC: return "non-finite state";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+    case LBM_ERR_STATE: return "invalid state";
+    case LBM_ERR_UNSUPPORTED: return "unsupported combination";
+    }
+    return "unknown status";
+}
+
+lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) { return create_batch(1, cfg, out); }
+
+lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_ctx** out)
+{
+    if (!cfgs) return LBM_ERR_INVALID_ARG;
+    return create_batch(n, cfgs, out);
+}
+
+void lbm_destroy(lbm_ctx* ctx)
+{
+    if (!ctx) return;
+    Batch* b = ctx->b;
+    delete ctx;
+    if (--b->refs == 0) destroy_batch(b);
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->b->err.c_str();
+}
+
+#define ENTER(ctx)                                    \
+    if (!(ctx)) return LBM_ERR_INVALID_ARG;           \
+    Batch* b = (ctx)->b;                              \
+    Instance& I = b->inst[(ctx)->idx];                \
+    (void)I;                                          \
+    if (b->status != LBM_OK) return b->status;
+
+lbm_status lbm_set_inflow(lbm_ctx* ctx, const lbm_inflow* in)
+{
+    ENTER(ctx);
+    if (!in || (in->kind != 0 && in->kind != 1)) return fail(b, LBM_ERR_INVALID_ARG, "bad inflow", false);
+    if (in->kind == 1 && !(in->z0 > 0.0 && in->z_ref > in->z0))
+        return fail(b, LBM_ERR_INVALID_ARG, "log law needs 0 < z0 < z_ref", false);
+    for (int a = 0; a < 3; ++a) I.h.u_ref[a] = in->u_ref[a];
+    I.h.inflow_kind = in->kind;
+    I.h.z0 = in->kind == 1 ? in->z0 : 0.1;
+    I.h.inv_log_zref_z0 = in->kind == 1 ? 1.0 / std::log(in->z_ref / in->z0) : 1.0;
+    const double U0 = std::sqrt(in->u_ref[0] * in->u_ref[0] + in->u_ref[1] * in->u_ref[1] + in->u_ref[2] * in->u_ref[2]);
+    I.h.noise_amp = in->noise_rel * U0;
+    b->dirty = true;
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    const int par = (int)(b->host_step & 1);
+    CK(launch_init(b->store, b->d_dom + ctx->idx, I.h, nullptr, nullptr, nullptr, par, 1, b->stream));
+    s = zero_fbox(b, I);
+    if (s != LBM_OK) return s;
+    return refresh_alm(b);
+}
+
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, const float* fneq)
+{
+    ENTER(ctx);
+    const long long N = I.h.N;
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    std::vector<float> hd, hu;
+    float *d_drho = nullptr, *d_u = nullptr, *d_fneq = nullptr;
+    if (rho) {
+        hd.resize(N);
+        for (long long i = 0; i < N; ++i) hd[i] = (float)(rho[i] - 1.0);
+        d_drho = (float*)dalloc(b, sizeof(float) * N);
+        if (!d_drho) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+        CK(cudaMemcpyAsync(d_drho, hd.data(), sizeof(float) * N, cudaMemcpyHostToDevice, b->stream));
+    }
+    if (u) {
+        hu.resize(3 * N);
+        for (long long i = 0; i < 3 * N; ++i) hu[i] = (float)u[i];
+        d_u = (float*)dalloc(b, sizeof(float) * 3 * N);
+        if (!d_u) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+        CK(cudaMemcpyAsync(d_u, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice, b->stream));
+    }
+    if (fneq) {
+        d_fneq = (float*)dalloc(b, sizeof(float) * 27 * N);
+        if (!d_fneq) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+        CK(cudaMemcpyAsync(d_fneq, fneq, sizeof(float) * 27 * N, cudaMemcpyHostToDevice, b->stream));
+    }
+    const int par = (int)(b->host_step & 1);
+    CK(launch_init(b->store, b->d_dom + ctx->idx, I.h, d_drho, d_u, d_fneq, par, 1, b->stream));
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    else CK(cudaDeviceSynchronize());
+    dfree(b, d_drho);
+    dfree(b, d_u);
+    dfree(b, d_fneq);
+    s = zero_fbox(b, I);
+    if (s != LBM_OK) return s;
+    return refresh_alm(b);
+}
+
+lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
+{
+    ENTER(ctx);
+    if (!d) return fail(b, LBM_ERR_INVALID_ARG, "null turbine", false);
+    if ((int)I.turb.size() >= kMaxTurbines) return fail(b, LBM_ERR_INVALID_ARG, "too many rotors", false);
+    if (d->n_blades < 1 || d->n_elements < 1 || I.h.n_el + d->n_blades * d->n_elements > kMaxElements)
+        return fail(b, LBM_ERR_INVALID_ARG, "element count out of range", false);
+    if (!(d->epsilon >= 0.5 && d->epsilon <= 5.0)) return fail(b, LBM_ERR_INVALID_ARG, "epsilon must be in [0.5, 5]", false);
+    if (!(d->radius > 0.0)) return fail(b, LBM_ERR_INVALID_ARG, "radius must be > 0", false);
+    if (d->n_polar < 2 || !d->alpha || !d->cl || !d->cd) return fail(b, LBM_ERR_INVALID_ARG, "polar table missing", false);
+    for (int i = 1; i < d->n_polar; ++i)
+        if (!(d->alpha[i] > d->alpha[i - 1])) return fail(b, LBM_ERR_INVALID_ARG, "alpha must ascend", false);
+    TurbineHost t;
+    t.desc = *d;
+    t.alpha.assign(d->alpha, d->alpha + d->n_polar);
+    t.cl.assign(d->cl, d->cl + d->n_polar);
+    t.cd.assign(d->cd, d->cd + d->n_polar);
+    if (d->twist) t.twist.assign(d->twist, d->twist + d->n_elements);
+    DevTurbine& B = t.dev;
+    const double cy = std::cos(d->yaw), sy = std::sin(d->yaw);
+    const double ea[3] = {cy, sy, 0.0}, e1[3] = {-sy, cy, 0.0}, e2[3] = {0.0, 0.0, 1.0};
+    const int n[3] = {I.h.nx, I.h.ny, I.h.nz};
+    const double cut = 3.0 * d->epsilon;
+    for (int a = 0; a < 3; ++a) {
+        B.hub[a] = (float)d->hub[a];
+        B.e_axis[a] = (float)ea[a];
+        B.e1[a] = (float)e1[a];
+        B.e2[a] = (float)e2[a];
+        const double ext = d->radius * std::sqrt(std::max(0.0, 1.0 - ea[a] * ea[a])) + cut + 1.0;
+        B.lo[a] = (int)std::floor(d->hub[a] - ext);
+        B.hi[a] = (int)std::ceil(d->hub[a] + ext);
+        if (B.lo[a] < 1 || B.hi[a] > n[a] - 2)
+            return fail(b, LBM_ERR_INVALID_ARG, "rotor force support must lie inside [1, n-2] on every axis", false);
+    }
+    B.radius = (float)d->radius;
+    B.n_blades = d->n_blades;
+    B.n_elements = d->n_elements;
+    B.eps = (float)d->epsilon;
+    B.inv_eps2 = (float)(1.0 / (d->epsilon * d->epsilon));
+    B.cut = (float)cut;
+    B.omega = d->omega;
+    B.theta0 = d->theta0;
+    B.pitch = (float)d->pitch;
+    B.chord_root = (float)d->chord_root;
+    B.chord_tip = (float)d->chord_tip;
+    B.n_polar = d->n_polar;
+    {
+        // equally spaced angles (to 1e-6 of the spacing): direct segment index on the device
+        const double da = (d->alpha[d->n_polar - 1] - d->alpha[0]) / (d->n_polar - 1);
+        bool uni = da > 0.0;
+        for (int i = 1; i < d->n_polar && uni; ++i)
+            if (std::fabs((d->alpha[i] - d->alpha[i - 1]) - da) > 1e-6 * da) uni = false;
+        B.polar_uniform = uni ? 1 : 0;
+        B.polar_a0 = (float)d->alpha[0];
+        B.polar_inv_da = uni ? (float)(1.0 / da) : 0.0f;
+    }
+    B.bnx = B.hi[0] - B.lo[0] + 1;
+    B.bny = B.hi[1] - B.lo[1] + 1;
+    B.bcells = (long long)B.bnx * B.bny * (B.hi[2] - B.lo[2] + 1);
+    B.el_offset = I.h.n_el;
+    std::vector<float> tab;
+    for (double v : t.alpha) tab.push_back((float)v);
+    for (double v : t.cl) tab.push_back((float)v);
+    for (double v : t.cd) tab.push_back((float)v);
+    for (double v : t.twist) tab.push_back((float)v);
+    float* d_tab = (float*)dalloc(b, sizeof(float) * tab.size());
+    float* d_fbox = (float*)dalloc(b, sizeof(float) * 3 * B.bcells);
+    if (!d_tab || !d_fbox) return fail(b, LBM_ERR_OOM, "rotor table allocation failed");
+    CK(cudaMemcpyAsync(d_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemsetAsync(d_fbox, 0, sizeof(float) * 3 * B.bcells, b->stream));
+    B.alpha = d_tab;
+    B.cl = d_tab + d->n_polar;
+    B.cd = d_tab + 2 * d->n_polar;
+    B.twist = d->twist ? d_tab + 3 * d->n_polar : nullptr;
+    B.fbox = d_fbox;
+    I.turb.push_back(std::move(t));
+    I.h.n_turb = (int)I.turb.size();
+    I.h.n_el += d->n_blades * d->n_elements;
+    if (id_out) *id_out = (int)I.turb.size() - 1;
+    b->dirty = true;
+    lbm_status s = refresh_alm(b);
+    if (s != LBM_OK) return s;
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    else CK(cudaDeviceSynchronize());
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
+{
+    ENTER(ctx);
+    if (n_steps < 0) return fail(b, LBM_ERR_INVALID_ARG, "n_steps < 0", false);
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    int left = n_steps;
+    if (b->profiling) {
+        for (; left > 0; --left) {
+            if (b->ev_used + 2 > b->ev.size()) {
+                if (b->ev.size() < 32768) {
+                    cudaEvent_t e0, e1;
+                    CK(cudaEventCreate(&e0));
+                    CK(cudaEventCreate(&e1));
+                    b->ev.push_back(e0);
+                    b->ev.push_back(e1);
+                } else {
+                    // fold the recorded pairs into the running sum and reuse the pool
+                    CK(cudaEventSynchronize(b->ev[b->ev_used - 1]));
+                    for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
+                        b->prof_ms += ms;
+                        b->prof_n++;
+                    }
+                    b->ev_used = 0;
+                }
+            }
+            CK(cudaEventRecord(b->ev[b->ev_used], b->stream));
+            s = launch_one(b, (int)(b->host_step & 1));
+            if (s != LBM_OK) return s;
+            CK(cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
+            b->ev_used += 2;
+            b->host_step++;
+        }
+        return LBM_OK;
+    }
+    if (b->stream && left >= 2) {
+        const int p = (int)(b->host_step & 1);
+        if (!b->gexec[p]) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            lbm_status s1 = launch_one(b, p);
+            lbm_status s2 = s1 == LBM_OK ? launch_one(b, p ^ 1) : s1;
+            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            if (s1 != LBM_OK || s2 != LBM_OK) return b->status;
+            CK(e);
+            e = cudaGraphInstantiate(&b->gexec[p], g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+        }
+        while (left >= 2) {
+            CK(cudaGraphLaunch(b->gexec[p], b->stream));
+            left -= 2;
+            b->host_step += 2;
+        }
+    }
+    for (; left > 0; --left) {
+        s = launch_one(b, (int)(b->host_step & 1));
+        if (s != LBM_OK) return s;
+        b->host_step++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* ctx)
+{
+    ENTER(ctx);
+    return check_device_errors(b);
+}
+
+lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u)
+{
+    ENTER(ctx);
+    if (!rho || !u) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    const long long N = I.h.N;
+    double* d = (double*)dalloc(b, sizeof(double) * 4 * N);
+    if (!d) return fail(b, LBM_ERR_OOM, "moment buffer allocation failed");
+    CK(launch_moments(b->store, b->d_dom + ctx->idx, I.h, (int)(b->host_step & 1), d, d + N, b->stream));
+    CK(cudaMemcpyAsync(rho, d, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(u, d + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, b->stream));
+    s = check_device_errors(b);
+    dfree(b, d);
+    return s;
+}
+
+lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f)
+{
+    ENTER(ctx);
+    if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    const long long N = I.h.N;
+    const void* src = I.h.f[b->host_step & 1];
+    std::vector<float> hf((size_t)27 * N);
+    if (b->store == STORE_FP32) {
+        CK(cudaMemcpyAsync(hf.data(), src, sizeof(float) * 27 * N, cudaMemcpyDeviceToHost, b->stream));
+    } else {
+        float* d = (float*)dalloc(b, sizeof(float) * 27 * N);
+        if (!d) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+        CK(launch_to_float(b->store, src, d, 27 * N, b->stream));
+        CK(cudaMemcpyAsync(hf.data(), d, sizeof(float) * 27 * N, cudaMemcpyDeviceToHost, b->stream));
+        lbm_status s = check_device_errors(b);
+        dfree(b, d);
+        if (s != LBM_OK) return s;
+    }
+    lbm_status s = check_device_errors(b);
+    if (s != LBM_OK) return s;
+    for (int q = 0; q < 27; ++q) {
+        const double w = wqh(q);
+        for (long long i = 0; i < N; ++i) f[(size_t)q * N + i] = w + (double)hf[(size_t)q * N + i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f)
+{
+    ENTER(ctx);
+    if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null input", false);
+    const long long N = I.h.N;
+    std::vector<float> hf((size_t)27 * N);
+    for (int q = 0; q < 27; ++q) {
+        const double w = wqh(q);
+        for (long long i = 0; i < N; ++i) hf[(size_t)q * N + i] = (float)(f[(size_t)q * N + i] - w);
+    }
+    void* dst = I.h.f[b->host_step & 1];
+    if (b->store == STORE_FP32) {
+        CK(cudaMemcpyAsync(dst, hf.data(), sizeof(float) * 27 * N, cudaMemcpyHostToDevice, b->stream));
+        if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    } else {
+        float* d = (float*)dalloc(b, sizeof(float) * 27 * N);
+        if (!d) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+        CK(cudaMemcpyAsync(d, hf.data(), sizeof(float) * 27 * N, cudaMemcpyHostToDevice, b->stream));
+        CK(launch_from_float(b->store, d, dst, 27 * N, b->stream));
+        if (b->stream) CK(cudaStreamSynchronize(b->stream));
+        else CK(cudaDeviceSynchronize());
+        dfree(b, d);
+    }
+    return refresh_alm(b);
+}
+
+lbm_status alm_get_loads(lbm_ctx* ctx, int id, double* thrust, double* torque, float* elem_force, float* elem_pos)
+{
+    ENTER(ctx);
+    if (id < 0 || id >= (int)I.turb.size()) return fail(b, LBM_ERR_INVALID_ARG, "bad rotor id", false);
+    lbm_status s = check_device_errors(b);
+    if (s != LBM_OK) return s;
+    const int par = b->host_step > 0 ? (int)((b->host_step - 1) & 1) : 0;
+    double L[2];
+    CK(cudaMemcpy(L, I.h.loads[par] + 2 * id, sizeof L, cudaMemcpyDeviceToHost));
+    if (thrust) *thrust = L[0];
+    if (torque) *torque = L[1];
+    const DevTurbine& B = I.turb[id].dev;
+    const int ne = B.n_blades * B.n_elements;
+    std::vector<float4> tmp(ne);
+    if (elem_force) {
+        CK(cudaMemcpy(tmp.data(), I.h.el_force[par] + B.el_offset, sizeof(float4) * ne, cudaMemcpyDeviceToHost));
+        for (int e = 0; e < ne; ++e) {
+            elem_force[3 * e] = tmp[e].x;
+            elem_force[3 * e + 1] = tmp[e].y;
+            elem_force[3 * e + 2] = tmp[e].z;
+        }
+    }
+    if (elem_pos) {
+        CK(cudaMemcpy(tmp.data(), I.h.el_pos[par] + B.el_offset, sizeof(float4) * ne, cudaMemcpyDeviceToHost));
+        for (int e = 0; e < ne; ++e) {
+            elem_pos[3 * e] = tmp[e].x;
+            elem_pos[3 * e + 1] = tmp[e].y;
+            elem_pos[3 * e + 2] = tmp[e].z;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_step)
+{
+    ENTER(ctx);
+    if (!mass_mom) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    lbm_status s = check_device_errors(b);
+    if (s != LBM_OK) return s;
+    double r[5];
+    CK(cudaMemcpy(r, I.h.diag_res, sizeof r, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; ++k) mass_mom[k] = r[k];
+    if (at_step) *at_step = (long long)r[4];
+    return LBM_OK;
+}
+
+lbm_status lbm_get_step(lbm_ctx* ctx, long long* step)
+{
+    ENTER(ctx);
+    if (!step) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    *step = b->host_step;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_step(lbm_ctx* ctx, long long step)
+{
+    ENTER(ctx);
+    if (step < 0) return fail(b, LBM_ERR_INVALID_ARG, "step < 0", false);
+    if ((step & 1) != (b->host_step & 1)) {
+        // keep the live state in array f[step & 1]
+        for (auto& In : b->inst) std::swap(In.h.f[0], In.h.f[1]);
+        b->dirty = true;
+    }
+    b->host_step = step;
+    CK(cudaMemcpyAsync(b->d_step + (step & 1), &b->host_step, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    lbm_status s = refresh_alm(b);
+    if (s != LBM_OK) return s;
+    return check_device_errors(b);
+}
+
+lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable)
+{
+    ENTER(ctx);
+    b->profiling = enable != 0;
+    b->ev_used = 0;
+    b->prof_ms = 0.0;
+    b->prof_n = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches)
+{
+    ENTER(ctx);
+    if (b->ev_used > 0) {
+        CK(cudaEventSynchronize(b->ev[b->ev_used - 1]));
+        for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
+            b->prof_ms += ms;
+            b->prof_n++;
+        }
+        b->ev_used = 0;
+    }
+    if (mean_ms) *mean_ms = b->prof_n ? b->prof_ms / (double)b->prof_n : 0.0;
+    if (launches) *launches = b->prof_n;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_launch)
+{
+    ENTER(ctx);
+    if (bytes_per_cell) *bytes_per_cell = 54.0 * (double)store_bytes(b->store);
+    long long cells = 0;
+    for (auto& In : b->inst) cells += In.h.N;
+    if (cells_per_launch) *cells_per_launch = cells;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal descriptors shared by the CUDA kernels (lbm_kernels.cu) and the
+// host runtime behind the C ABI (lbm_abi.cu).  Plain old data only: these
+// structs are copied to device memory as they are.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbmgb {
+
+constexpr int kMaxTurbines = 16;    // rotors per lattice
+constexpr int kMaxElements = 4096;  // blade elements per lattice
+constexpr int kMaxInstances = 64;   // lattices per batch
+
+enum Bc : int { BC_PERIODIC = 0, BC_INOUT = 1, BC_NOSLIP = 2 };
+enum Coll : int { COLL_CUMULANT = 0, COLL_SRT_SMAG = 1 };
+enum Store : int { STORE_FP32 = 0, STORE_BF16 = 1, STORE_FP16 = 2 };
+
+// Device error bits (DevDomain::err).
+enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_ELEMENT_OUTSIDE = 2u };
+
+// One rotor.  Rotor basis: e_axis = (cos yaw, sin yaw, 0), e1 = (-sin yaw,
+// cos yaw, 0), e2 = (0, 0, 1); blade direction e_r = cos(theta) e1 + sin(theta) e2.
+struct DevTurbine {
+    float hub[3];
+    float radius;
+    int n_blades, n_elements;
+    float eps, inv_eps2, cut;  // Gaussian width, 1/eps^2, cut-off 3 eps
+    double omega, theta0;      // rad per step, rad
+    float e_axis[3], e1[3], e2[3];
+    float pitch, chord_root, chord_tip;
+    const float* twist;        // n_elements or nullptr
+    int n_polar;
+    const float* alpha;
+    const float* cl;
+    const float* cd;
+    int polar_uniform;         // alpha equally spaced: direct segment index
+    float polar_a0, polar_inv_da;
+    int lo[3], hi[3];          // force box, inclusive cell bounds
+    int bnx, bny;              // box extents along x, y
+    long long bcells;          // cells in the box
+    float* fbox;               // ALM force of the last collision at the box cells, 3 planes
+    int el_offset;             // first element of this rotor in the lattice's element list
+};
+
+// One lattice.
+struct DevDomain {
+    int nx, ny, nz;
+    long long N;
+    int bc[3];
+    float omega;               // shear relaxation rate 1/(3 nu + 1/2)
+    float tau0;                // 3 nu + 1/2
+    float smag_c2;             // Smagorinsky C^2
+    float body[3];
+    int inflow_kind;           // 0 uniform, 1 log law
+    double u_ref[3];
+    double z0, inv_log_zref_z0;
+    double noise_amp;          // noise_rel * |u_ref|
+    unsigned long long seed;
+    void* f[2];                // PDF offset arrays [27][nz][ny][nx] of the storage type
+    int n_turb;
+    DevTurbine* turb;          // device array of n_turb
+    float4* el_pos[2];         // by step parity: element position (xyz) and 1/(Sx Sy Sz) (w)
+    float4* el_force[2];       // by step parity: blade force (xyz)
+    double* el_load;           // scratch, 2 doubles per element
+    float4* el_corner;         // scratch, 8 corners x (rho, u) per element
+    double* loads[2];          // by step parity: thrust, torque per rotor
+    int n_el;
+    unsigned int* rotor_counter;
+    int n_rotor_tiles;
+    int diag_every;
+    double* diag_acc;          // 4 doubles, accumulated on a diagnostic step
+    double* diag_res;          // 4 doubles + the step they belong to
+    unsigned int* err;
+};
+
+// Arguments of one stream-collide launch over all lattices of a batch.
+struct StepArgs {
+    const DevDomain* dom;               // device array
+    const unsigned long long* tiles;    // work list
+    unsigned int n_tiles;
+    int n_inst;
+    int parity;                         // source array f[parity], destination f[parity ^ 1]
+    long long* step_slot;               // step n in slot [parity]; CTA 0 writes n+1 to slot [parity ^ 1]
+    unsigned int* diag_done;            // CTA completion counter, used on diagnostic steps only
+    int diag_every;                     // diagnostic period shared by the batch (0 = off)
+};
+
+// Work-list entry: bit 63 rotor tile, bits 48..62 instance, 32..47 z, 16..31 y0, 0..15 x0.
+__host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0, int x0, bool rotor)
+{
+    return ((unsigned long long)(rotor ? 1u : 0u) << 63) | ((unsigned long long)(inst & 0x7FFF) << 48) |
+           ((unsigned long long)(z & 0xFFFF) << 32) | ((unsigned long long)(y0 & 0xFFFF) << 16) |
+           (unsigned long long)(x0 & 0xFFFF);
+}
+
+// Host-side launchers (lbm_kernels.cu).
+cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a);
+cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
+cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const float* drho,
+                        const float* u, const float* fneq, int parity, int inflow_mean, cudaStream_t s);
+cudaError_t launch_moments(int store, const DevDomain* d_dom_inst, const DevDomain& h, int parity, double* rho,
+                           double* u, cudaStream_t s);
+cudaError_t launch_to_float(int store, const void* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_from_float(int store, const float* src, void* dst, long long n, cudaStream_t s);
+
+}  // namespace lbmgb

@@ -1,0 +1,881 @@
+// sm_103a kernels of the D3Q27 LBM + actuator line time step (arxiv 2402.13171).
+//
+// k_step: one fused pass per time step over every cell of every lattice of a
+// batch: pull streaming with boundary rules (Sec. 2.1, streaming step), force
+// (body force + Gaussian-regularised blade forces, Sec. 2.2, gathered in the
+// rotor box), collision (cumulant, Sec. 2.1 / Geier et al. 2015, or BGK with a
+// Smagorinsky eddy viscosity), store.  PDFs live in HBM as offsets h = f - w
+// in the storage type; all arithmetic is FP32.  The CTAs covering the rotor
+// boxes are first in the work list; the last of them to finish evaluates the
+// actuator line for the next step (blade kinematics of Algorithm 2, trilinear
+// sampling, blade-element forces, FP64 rotor loads) while the remaining CTAs
+// stream the bulk of the lattice, so a time step is a single launch.
+#include "lbm_internal.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace lbmgb {
+
+// ------------------------------------------------------------------ lattice
+
+__host__ __device__ constexpr int qcx(int q) { return q % 3 - 1; }
+__host__ __device__ constexpr int qcy(int q) { return (q / 3) % 3 - 1; }
+__host__ __device__ constexpr int qcz(int q) { return q / 9 - 1; }
+__host__ __device__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+__host__ __device__ constexpr float wq(int q) { return w1(qcx(q)) * w1(qcy(q)) * w1(qcz(q)); }
+
+// ------------------------------------------------------------------ storage
+
+template <typename T> struct Io;
+template <> struct Io<float> {
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Io<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct Io<__half> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// ------------------------------------------------------------------ inflow
+
+// splitmix64 (Steele, Lea, Flood 2014): k-th output of the generator started at `seed`.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long k)
+{
+    unsigned long long z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Inflow velocity of inlet column (y, z) at step n: mean profile + per-component
+// noise noise_amp * xi, xi in [-1, 1) from the top 53 bits; FP64, rounded to FP32.
+__device__ void inflow_velocity(const DevDomain* D, long long step, int y, int z, float u[3])
+{
+    double scale = 1.0;
+    if (D->inflow_kind == 1) scale = log((z + 0.5) / D->z0) * D->inv_log_zref_z0;
+    for (int a = 0; a < 3; ++a) {
+        unsigned long long counter =
+            (((unsigned long long)step * (unsigned long long)D->nz + (unsigned long long)z) * (unsigned long long)D->ny +
+             (unsigned long long)y) * 3ull + (unsigned long long)a;
+        unsigned long long r = splitmix64(D->seed, counter + 1ull);
+        double xi = (double)(r >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        u[a] = (float)(D->u_ref[a] * scale + D->noise_amp * xi);
+    }
+}
+
+// ------------------------------------------------------------------ equilibrium
+
+// Per-axis factors of the product equilibrium, split as phi = w1 + dphi with
+// dphi(0) = -u^2, dphi(+-1) = (u^2 +- u)/2 (index c+1).
+__device__ __forceinline__ void axis_factors(float u, float ph[3], float dp[3])
+{
+    float u2 = u * u;
+    dp[0] = 0.5f * (u2 - u);
+    dp[1] = -u2;
+    dp[2] = 0.5f * (u2 + u);
+    ph[0] = w1(-1) + dp[0];
+    ph[1] = w1(0) + dp[1];
+    ph[2] = w1(1) + dp[2];
+}
+
+// out[q] = feq_q(1 + drho, u) - w_q, evaluated as a telescoped product so the
+// result carries the absolute precision of the small terms.
+__device__ __forceinline__ void feq_offsets(float drho, float ux, float uy, float uz, float out[27])
+{
+    float px[3], dx[3], py[3], dy[3], pz[3], dz[3];
+    axis_factors(ux, px, dx);
+    axis_factors(uy, py, dy);
+    axis_factors(uz, pz, dz);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float P = py[j] * pz[k];
+            const float Dd = dy[j] * pz[k] + w1(j - 1) * dz[k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float A = fmaf(drho, px[i], dx[i]);
+                out[k * 9 + j * 3 + i] = fmaf(A, P, w1(i - 1) * Dd);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float feq_offset_one(int q, float ux, float uy, float uz)
+{
+    float px[3], dx[3], py[3], dy[3], pz[3], dz[3];
+    axis_factors(ux, px, dx);
+    axis_factors(uy, py, dy);
+    axis_factors(uz, pz, dz);
+    const int i = q % 3, j = (q / 3) % 3, k = q / 9;
+    return dx[i] * py[j] * pz[k] + w1(i - 1) * (dy[j] * pz[k] + w1(j - 1) * dz[k]);
+}
+
+// ------------------------------------------------------------------ moments
+
+struct Moments {
+    float drho, jx, jy, jz, Sxx, Syy, Szz, Sxy, Sxz, Syz;
+};
+
+// Raw moments of the offsets up to second order, summed axis by axis.
+__device__ __forceinline__ Moments raw_moments(const float h[27])
+{
+    float m0[9], m1[9], m2[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const float a = h[3 * r], b = h[3 * r + 1], c = h[3 * r + 2];
+        m0[r] = a + b + c;
+        m1[r] = c - a;
+        m2[r] = c + a;
+    }
+    float A00[3], A10[3], A20[3], A01[3], A11[3], A02[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int r0 = 3 * k, r1 = 3 * k + 1, r2 = 3 * k + 2;
+        A00[k] = m0[r0] + m0[r1] + m0[r2];
+        A10[k] = m1[r0] + m1[r1] + m1[r2];
+        A20[k] = m2[r0] + m2[r1] + m2[r2];
+        A01[k] = m0[r2] - m0[r0];
+        A11[k] = m1[r2] - m1[r0];
+        A02[k] = m0[r2] + m0[r0];
+    }
+    Moments M;
+    M.drho = A00[0] + A00[1] + A00[2];
+    M.jx = A10[0] + A10[1] + A10[2];
+    M.jy = A01[0] + A01[1] + A01[2];
+    M.jz = A00[2] - A00[0];
+    M.Sxx = A20[0] + A20[1] + A20[2];
+    M.Syy = A02[0] + A02[1] + A02[2];
+    M.Szz = A00[2] + A00[0];
+    M.Sxy = A11[0] + A11[1] + A11[2];
+    M.Sxz = A10[2] - A10[0];
+    M.Syz = A01[2] - A01[0];
+    return M;
+}
+
+// ------------------------------------------------------------------ collisions
+
+// One-dimensional map from central moments (k0, k1, k2) about u to the three
+// populations at c = -1, 0, +1.
+__device__ __forceinline__ void inv1d(float u, float k0, float k1, float k2, float& fm, float& f0, float& fp)
+{
+    const float u2 = u * u;
+    f0 = (1.0f - u2) * k0 - 2.0f * u * k1 - k2;
+    fm = 0.5f * ((u2 - u) * k0 + (2.0f * u - 1.0f) * k1 + k2);
+    fp = 0.5f * ((u2 + u) * k0 + (2.0f * u + 1.0f) * k1 + k2);
+}
+
+// Cumulant collision with shear rate omega, bulk and all higher-order rates 1
+// (all cumulants above second order relax to zero, so post-collision central
+// moments of order 4 and 6 are the Gaussian products of the second-order ones,
+// orders 3 and 5 vanish), forcing by the velocity shift (first central moments
+// -F/2 -> +F/2).  Computed as h* = (feq(rho, u) - w) + L_u(Delta), Delta the
+// post-collision central moments minus those of the product equilibrium.
+__device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy, float Fz, float omega, float& drho_o,
+                                                 float& jx_o, float& jy_o, float& jz_o)
+{
+    const Moments M = raw_moments(h);
+    const float rho = 1.0f + M.drho;
+    const float inv = 1.0f / rho;
+    const float ux = (M.jx + 0.5f * Fx) * inv;
+    const float uy = (M.jy + 0.5f * Fy) * inv;
+    const float uz = (M.jz + 0.5f * Fz) * inv;
+    const float third = 1.0f / 3.0f;
+    // second central moments minus rho/3 delta
+    const float axx = M.Sxx - M.drho * third - rho * ux * ux + ux * Fx;
+    const float ayy = M.Syy - M.drho * third - rho * uy * uy + uy * Fy;
+    const float azz = M.Szz - M.drho * third - rho * uz * uz + uz * Fz;
+    const float axy = M.Sxy - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
+    const float axz = M.Sxz - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
+    const float ayz = M.Syz - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
+    const float om1 = 1.0f - omega;
+    const float tr3 = (axx + ayy + azz) * third;
+    const float bxx = om1 * (axx - tr3), byy = om1 * (ayy - tr3), bzz = om1 * (azz - tr3);
+    const float bxy = om1 * axy, bxz = om1 * axz, byz = om1 * ayz;
+
+    float D[27];
+#pragma unroll
+    for (int m = 0; m < 27; ++m) D[m] = 0.0f;
+#define MI(a, b, c) ((c) * 9 + (b) * 3 + (a))
+    D[MI(1, 0, 0)] = 0.5f * Fx;
+    D[MI(0, 1, 0)] = 0.5f * Fy;
+    D[MI(0, 0, 1)] = 0.5f * Fz;
+    D[MI(2, 0, 0)] = bxx;
+    D[MI(0, 2, 0)] = byy;
+    D[MI(0, 0, 2)] = bzz;
+    D[MI(1, 1, 0)] = bxy;
+    D[MI(1, 0, 1)] = bxz;
+    D[MI(0, 1, 1)] = byz;
+    D[MI(2, 2, 0)] = (bxx + byy) * third + (bxx * byy + 2.0f * bxy * bxy) * inv;
+    D[MI(2, 0, 2)] = (bxx + bzz) * third + (bxx * bzz + 2.0f * bxz * bxz) * inv;
+    D[MI(0, 2, 2)] = (byy + bzz) * third + (byy * bzz + 2.0f * byz * byz) * inv;
+    D[MI(2, 1, 1)] = byz * third + (bxx * byz + 2.0f * bxy * bxz) * inv;
+    D[MI(1, 2, 1)] = bxz * third + (byy * bxz + 2.0f * bxy * byz) * inv;
+    D[MI(1, 1, 2)] = bxy * third + (bzz * bxy + 2.0f * bxz * byz) * inv;
+    {
+        const float sxx = bxx * inv, syy = byy * inv, szz = bzz * inv;
+        const float sxy = bxy * inv, sxz = bxz * inv, syz = byz * inv;
+        const float g = (sxx + syy + szz) * (1.0f / 9.0f) + (sxx * syy + sxx * szz + syy * szz) * third +
+                        sxx * syy * szz + 2.0f * (third + sxx) * syz * syz + 2.0f * (third + syy) * sxz * sxz +
+                        2.0f * (third + szz) * sxy * sxy + 8.0f * sxy * sxz * syz;
+        D[MI(2, 2, 2)] = rho * g;
+    }
+#undef MI
+    // inverse transform about u: z, then y, then x
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float fm, f0, fp;
+            inv1d(uz, D[b * 3 + a], D[9 + b * 3 + a], D[18 + b * 3 + a], fm, f0, fp);
+            D[b * 3 + a] = fm;
+            D[9 + b * 3 + a] = f0;
+            D[18 + b * 3 + a] = fp;
+        }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float fm, f0, fp;
+            inv1d(uy, D[k * 9 + a], D[k * 9 + 3 + a], D[k * 9 + 6 + a], fm, f0, fp);
+            D[k * 9 + a] = fm;
+            D[k * 9 + 3 + a] = f0;
+            D[k * 9 + 6 + a] = fp;
+        }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        float fm, f0, fp;
+        inv1d(ux, D[3 * r], D[3 * r + 1], D[3 * r + 2], fm, f0, fp);
+        D[3 * r] = fm;
+        D[3 * r + 1] = f0;
+        D[3 * r + 2] = fp;
+    }
+    float E[27];
+    feq_offsets(M.drho, ux, uy, uz, E);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) h[q] = E[q] + D[q];
+    drho_o = M.drho;
+    jx_o = M.jx + Fx;
+    jy_o = M.jy + Fy;
+    jz_o = M.jz + Fz;
+}
+
+// BGK toward the polynomial equilibrium with a Smagorinsky eddy viscosity
+// (tau = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C^2 |Pi|/rho))/2, Pi the
+// force-corrected non-equilibrium momentum flux) and the Guo source
+// (1 - omega/2) w [3(c - u) + 9 (c.u) c].F.
+__device__ __forceinline__ void collide_srt_smag(float h[27], float Fx, float Fy, float Fz, float tau0, float smag_c2,
+                                                 float& drho_o, float& jx_o, float& jy_o, float& jz_o)
+{
+    const Moments M = raw_moments(h);
+    const float rho = 1.0f + M.drho;
+    const float inv = 1.0f / rho;
+    const float ux = (M.jx + 0.5f * Fx) * inv;
+    const float uy = (M.jy + 0.5f * Fy) * inv;
+    const float uz = (M.jz + 0.5f * Fz) * inv;
+    const float third = 1.0f / 3.0f;
+    const float axx = M.Sxx - M.drho * third - rho * ux * ux + ux * Fx;
+    const float ayy = M.Syy - M.drho * third - rho * uy * uy + uy * Fy;
+    const float azz = M.Szz - M.drho * third - rho * uz * uz + uz * Fz;
+    const float axy = M.Sxy - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
+    const float axz = M.Sxz - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
+    const float ayz = M.Syz - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
+    const float P2 = axx * axx + ayy * ayy + azz * azz + 2.0f * (axy * axy + axz * axz + ayz * ayz);
+    const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + 18.0f * 1.41421356237f * smag_c2 * sqrtf(P2) * inv));
+    const float om = 1.0f / tau;
+    const float src = 1.0f - 0.5f * om;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const float cx = (float)qcx(q), cy = (float)qcy(q), cz = (float)qcz(q);
+        const float cu = cx * ux + cy * uy + cz * uz;
+        const float cF = cx * Fx + cy * Fy + cz * Fz;
+        const float feq = wq(q) * (M.drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+        const float S = src * wq(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);
+        h[q] = h[q] - om * (h[q] - feq) + S;
+    }
+    drho_o = M.drho;
+    jx_o = M.jx + Fx;
+    jy_o = M.jy + Fy;
+    jz_o = M.jz + Fz;
+}
+
+// ------------------------------------------------------------------ streaming
+
+__device__ __forceinline__ long long cell_of(const DevDomain* D, int x, int y, int z)
+{
+    return ((long long)z * D->ny + y) * D->nx + x;
+}
+
+// Pre-collision population q of cell (x, y, z) by the general boundary rules:
+// no-slip (halfway bounce-back) first, then periodic wrap, then the x inlet
+// (equilibrium at rho = 1 and the inflow velocity of the source column) and
+// outlet (source moved to the last plane).
+template <typename T, bool CG>
+__device__ float pull_general(const DevDomain* D, const T* f, int q, int x, int y, int z, long long step)
+{
+    const int c[3] = {qcx(q), qcy(q), qcz(q)};
+    const int n[3] = {D->nx, D->ny, D->nz};
+    int s[3] = {x - c[0], y - c[1], z - c[2]};
+    bool wall = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (D->bc[a] == BC_NOSLIP && (s[a] < 0 || s[a] >= n[a])) wall = true;
+    const T* p;
+    if (wall) {
+        p = f + (size_t)(26 - q) * D->N + cell_of(D, x, y, z);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (D->bc[a] == BC_PERIODIC) s[a] = s[a] < 0 ? s[a] + n[a] : (s[a] >= n[a] ? s[a] - n[a] : s[a]);
+        if (D->bc[0] == BC_INOUT) {
+            if (s[0] < 0) {
+                float u[3];
+                inflow_velocity(D, step, s[1], s[2], u);
+                return feq_offset_one(q, u[0], u[1], u[2]);
+            }
+            if (s[0] >= n[0]) s[0] = n[0] - 1;
+        }
+        p = f + (size_t)q * D->N + cell_of(D, s[0], s[1], s[2]);
+    }
+    return CG ? Io<T>::ldcg(p) : Io<T>::ld(p);
+}
+
+// ------------------------------------------------------------------ actuator line
+
+// Segment of an ascending table containing x (x strictly inside the range):
+// direct index for equally spaced tables, bisection otherwise.
+__device__ __forceinline__ int table_segment(const DevTurbine* B, float x)
+{
+    const float* xs = B->alpha;
+    const int n = B->n_polar;
+    int lo;
+    if (B->polar_uniform) {
+        lo = (int)floorf((x - B->polar_a0) * B->polar_inv_da);
+        lo = lo < 0 ? 0 : (lo > n - 2 ? n - 2 : lo);
+        while (lo > 0 && xs[lo] > x) --lo;
+        while (lo < n - 2 && xs[lo + 1] < x) ++lo;
+    } else {
+        lo = 0;
+        int hi = n - 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (xs[mid] <= x) lo = mid; else hi = mid;
+        }
+    }
+    return lo;
+}
+
+// C_L and C_D at angle of attack x: linear interpolation, clamped at the ends.
+__device__ __forceinline__ void polar_lookup(const DevTurbine* B, float x, float& CL, float& CD)
+{
+    const float* xs = B->alpha;
+    const int n = B->n_polar;
+    if (x <= xs[0]) { CL = B->cl[0]; CD = B->cd[0]; return; }
+    if (x >= xs[n - 1]) { CL = B->cl[n - 1]; CD = B->cd[n - 1]; return; }
+    const int lo = table_segment(B, x);
+    const float t = (x - xs[lo]) / (xs[lo + 1] - xs[lo]);
+    CL = B->cl[lo] + t * (B->cl[lo + 1] - B->cl[lo]);
+    CD = B->cd[lo] + t * (B->cd[lo + 1] - B->cd[lo]);
+}
+
+// Sum of the ALM force boxes containing cell (x, y, z) (written by this or the
+// previous launch; read through L2).
+__device__ __forceinline__ void alm_box_force(const DevDomain* D, int x, int y, int z, float F[3])
+{
+    for (int t = 0; t < D->n_turb; ++t) {
+        const DevTurbine* B = D->turb + t;
+        if (x < B->lo[0] || x > B->hi[0] || y < B->lo[1] || y > B->hi[1] || z < B->lo[2] || z > B->hi[2]) continue;
+        const long long bi = ((long long)(z - B->lo[2]) * B->bny + (y - B->lo[1])) * B->bnx + (x - B->lo[0]);
+        F[0] += __ldcg(B->fbox + bi);
+        F[1] += __ldcg(B->fbox + B->bcells + bi);
+        F[2] += __ldcg(B->fbox + 2 * B->bcells + bi);
+    }
+}
+
+// Geometry of blade element g at step n (Algorithm 2 for a hub + straight
+// blades): blade angle theta = theta0 + omega n + 2 pi b / B accumulated in
+// FP64 from the integer step and reduced mod 2 pi, then FP32.
+struct ElementGeo {
+    const DevTurbine* B;
+    int k;
+    float r, len;
+    float p[3], v[3], er[3], et[3];
+};
+
+__device__ __forceinline__ void element_geometry(const DevDomain* D, int g, long long step, ElementGeo& G)
+{
+    int t = 0;
+    while (t + 1 < D->n_turb && D->turb[t + 1].el_offset <= g) ++t;
+    const DevTurbine* B = D->turb + t;
+    const int le = g - B->el_offset;
+    const int b = le / B->n_elements;
+    G.B = B;
+    G.k = le - b * B->n_elements;
+    double th = B->theta0 + B->omega * (double)step + 6.283185307179586 * (double)b / (double)B->n_blades;
+    th = fmod(th, 6.283185307179586);
+    float sn, cs;
+    sincosf((float)th, &sn, &cs);
+    const float* ea = B->e_axis;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) G.er[a] = cs * B->e1[a] + sn * B->e2[a];
+    G.et[0] = ea[1] * G.er[2] - ea[2] * G.er[1];
+    G.et[1] = ea[2] * G.er[0] - ea[0] * G.er[2];
+    G.et[2] = ea[0] * G.er[1] - ea[1] * G.er[0];
+    G.len = B->radius / (float)B->n_elements;
+    G.r = ((float)G.k + 0.5f) * G.len;
+    const float om = (float)B->omega;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        G.p[a] = B->hub[a] + G.r * G.er[a];
+        G.v[a] = om * G.r * G.et[a];
+    }
+}
+
+// Actuator line of step `step` for one lattice, by the whole CTA.  Reads the
+// populations of the current array f (post-collision of step-1) and the box
+// force of step-1; writes element positions with their spreading
+// normalisation, blade forces, and per-rotor FP64 thrust and torque into the
+// buffers of parity step & 1.
+//  phase 1, one thread per (element, corner): pull the 27 populations of the
+//    corner cell, rho and u = (sum c f + F/2)/rho at the corner;
+//  phase 2, one thread per element: trilinear blend, relative velocity,
+//    angle of attack, polars, blade force, Gaussian normalisation, FP64 loads;
+//  phase 3, warp 0: per-rotor FP64 sums in a fixed order.
+template <typename T>
+__device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long long step)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int par = (int)(step & 1);
+    const long long N = D->N;
+    const int n[3] = {D->nx, D->ny, D->nz};
+    for (int pc = tid; pc < 8 * D->n_el; pc += nthr) {
+        const int g = pc >> 3, cn = pc & 7;
+        ElementGeo G;
+        element_geometry(D, g, step, G);
+        int c[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int i0 = (int)floorf(G.p[a]);
+            if (i0 < 1 || i0 + 1 > n[a] - 2) inside = false;
+            c[a] = i0 + ((cn >> a) & 1);
+        }
+        float4 out = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        if (inside) {
+            float h[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q)
+                h[q] = Io<T>::ldcg(f + (size_t)q * N + cell_of(D, c[0] - qcx(q), c[1] - qcy(q), c[2] - qcz(q)));
+            float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                drho += h[q];
+                jx += (float)qcx(q) * h[q];
+                jy += (float)qcy(q) * h[q];
+                jz += (float)qcz(q) * h[q];
+            }
+            float F[3] = {D->body[0], D->body[1], D->body[2]};
+            alm_box_force(D, c[0], c[1], c[2], F);
+            const float rho = 1.0f + drho;
+            out = make_float4(rho, (jx + 0.5f * F[0]) / rho, (jy + 0.5f * F[1]) / rho, (jz + 0.5f * F[2]) / rho);
+        } else if (cn == 0) {
+            atomicOr(D->err, ERR_ELEMENT_OUTSIDE);
+        }
+        D->el_corner[pc] = out;
+    }
+    __syncthreads();
+    for (int g = tid; g < D->n_el; g += nthr) {
+        ElementGeo G;
+        element_geometry(D, g, step, G);
+        const DevTurbine* B = G.B;
+        float fr[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fr[a] = G.p[a] - floorf(G.p[a]);
+        float rho_p = 0.f, u_p[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int cn = 0; cn < 8; ++cn) {
+            const float w = ((cn & 1) ? fr[0] : 1.0f - fr[0]) * (((cn >> 1) & 1) ? fr[1] : 1.0f - fr[1]) *
+                            (((cn >> 2) & 1) ? fr[2] : 1.0f - fr[2]);
+            const float4 q = D->el_corner[8 * g + cn];
+            rho_p += w * q.x;
+            u_p[0] += w * q.y;
+            u_p[1] += w * q.z;
+            u_p[2] += w * q.w;
+        }
+        // relative velocity without its radial part, angle of attack, polars
+        const float* ea = B->e_axis;
+        float ur[3] = {u_p[0] - G.v[0], u_p[1] - G.v[1], u_p[2] - G.v[2]};
+        const float urad = ur[0] * G.er[0] + ur[1] * G.er[1] + ur[2] * G.er[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ur[a] -= urad * G.er[a];
+        const float uax = ur[0] * ea[0] + ur[1] * ea[1] + ur[2] * ea[2];
+        const float utan = ur[0] * G.et[0] + ur[1] * G.et[1] + ur[2] * G.et[2];
+        const float phi = atan2f(uax, -utan);
+        const float twist = B->twist ? B->twist[G.k] : 0.0f;
+        const float alpha = phi - twist - B->pitch;
+        float CL, CD;
+        polar_lookup(B, alpha, CL, CD);
+        const float chord = B->chord_root + (B->chord_tip - B->chord_root) * G.r / B->radius;
+        const float mag2 = ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2];
+        float Fb[3] = {0.0f, 0.0f, 0.0f};
+        if (mag2 > 0.0f) {
+            const float mag = sqrtf(mag2);
+            const float eD[3] = {ur[0] / mag, ur[1] / mag, ur[2] / mag};
+            const float eL[3] = {eD[1] * G.er[2] - eD[2] * G.er[1], eD[2] * G.er[0] - eD[0] * G.er[2],
+                                 eD[0] * G.er[1] - eD[1] * G.er[0]};
+            const float sc = 0.5f * rho_p * mag2 * chord * G.len;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Fb[a] = sc * (CL * eL[a] + CD * eD[a]);
+        }
+        // Gaussian normalisation: per-axis sums of exp(-(i - p)^2 / eps^2) over |i - p| <= 3 eps
+        float S = 1.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int lo = (int)ceilf(G.p[a] - B->cut), hi = (int)floorf(G.p[a] + B->cut);
+            float sa = 0.0f;
+            for (int i = lo; i <= hi; ++i) {
+                const float d = (float)i - G.p[a];
+                sa += expf(-d * d * B->inv_eps2);
+            }
+            S *= sa;
+        }
+        D->el_pos[par][g] = make_float4(G.p[0], G.p[1], G.p[2], 1.0f / S);
+        D->el_force[par][g] = make_float4(Fb[0], Fb[1], Fb[2], alpha);
+        D->el_load[2 * g] = (double)Fb[0] * ea[0] + (double)Fb[1] * ea[1] + (double)Fb[2] * ea[2];
+        D->el_load[2 * g + 1] =
+            (double)G.r * ((double)Fb[0] * G.et[0] + (double)Fb[1] * G.et[1] + (double)Fb[2] * G.et[2]);
+    }
+    __syncthreads();
+    if (tid < 32) {
+        for (int t = 0; t < D->n_turb; ++t) {
+            const DevTurbine* B = D->turb + t;
+            const int ne = B->n_blades * B->n_elements;
+            double th = 0.0, tq = 0.0;
+            for (int e = tid; e < ne; e += 32) {
+                th += D->el_load[2 * (B->el_offset + e)];
+                tq += D->el_load[2 * (B->el_offset + e) + 1];
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                th += __shfl_xor_sync(0xFFFFFFFFu, th, o);
+                tq += __shfl_xor_sync(0xFFFFFFFFu, tq, o);
+            }
+            if (tid == 0) {
+                D->loads[par][2 * t] = th;
+                D->loads[par][2 * t + 1] = tq;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ the time step
+
+template <int COLL, typename T>
+__global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
+{
+    __shared__ double s_red[8][4];
+    __shared__ int s_flag;
+    const unsigned long long tile = A.tiles[blockIdx.x];
+    const bool rotor_tile = (tile >> 63) != 0;
+    const int inst = (int)((tile >> 48) & 0x7FFF);
+    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
+    const int x = (int)(tile & 0xFFFF) + threadIdx.x;
+    const DevDomain* D = A.dom + inst;
+    const long long step = __ldcg(A.step_slot + A.parity);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) A.step_slot[A.parity ^ 1] = step + 1;
+    const int nx = D->nx, ny = D->ny, nz = D->nz;
+    const long long N = D->N;
+    const T* __restrict__ src = (const T*)D->f[A.parity];
+    T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
+    const bool diag = A.diag_every > 0 && (step % A.diag_every) == 0;  // uniform over the grid
+    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+
+    if (x < nx && y < ny) {
+        float h[27];
+        // neighbour coordinates and the fast/special decision
+        bool special = false;
+        int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+        const int bx = D->bc[0], by = D->bc[1], bz = D->bc[2];
+        if (bx == BC_PERIODIC) { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
+        else if (bx == BC_INOUT) { if (xm < 0) special = true; if (xp >= nx) xp = nx - 1; }
+        else { if (xm < 0 || xp >= nx) special = true; }
+        if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
+        else if (ym < 0 || yp >= ny) special = true;
+        if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
+        else if (zm < 0 || zp >= nz) special = true;
+        if (!special) {
+            const int xs[3] = {xp, x, xm};  // source x for cx = -1, 0, +1
+            const int ys[3] = {yp, y, ym};
+            const int zs[3] = {zp, z, zm};
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const long long sc = ((long long)zs[q / 9] * ny + ys[(q / 3) % 3]) * nx + xs[q % 3];
+                h[q] = Io<T>::ld(src + (size_t)q * N + sc);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) h[q] = pull_general<T, false>(D, src, q, x, y, z, step);
+        }
+        // force: body + regularised blade forces inside the rotor boxes
+        float F[3] = {D->body[0], D->body[1], D->body[2]};
+        if (rotor_tile) {
+            const float4* P = D->el_pos[step & 1];
+            const float4* Fe = D->el_force[step & 1];
+            for (int t = 0; t < D->n_turb; ++t) {
+                const DevTurbine* B = D->turb + t;
+                if (x < B->lo[0] || x > B->hi[0] || y < B->lo[1] || y > B->hi[1] || z < B->lo[2] || z > B->hi[2])
+                    continue;
+                const int ne = B->n_blades * B->n_elements;
+                const float cut = B->cut, ie2 = B->inv_eps2;
+                float ax = 0.0f, ay = 0.0f, az = 0.0f;
+                for (int e = 0; e < ne; ++e) {
+                    const float4 pe = __ldg(P + B->el_offset + e);
+                    const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
+                    if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
+                        const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
+                        const float4 fe = __ldg(Fe + B->el_offset + e);
+                        ax -= w * fe.x;
+                        ay -= w * fe.y;
+                        az -= w * fe.z;
+                    }
+                }
+                const long long bi = ((long long)(z - B->lo[2]) * B->bny + (y - B->lo[1])) * B->bnx + (x - B->lo[0]);
+                B->fbox[bi] = ax;
+                B->fbox[B->bcells + bi] = ay;
+                B->fbox[2 * B->bcells + bi] = az;
+                F[0] += ax;
+                F[1] += ay;
+                F[2] += az;
+            }
+        }
+        if (COLL == COLL_CUMULANT)
+            collide_cumulant(h, F[0], F[1], F[2], D->omega, o_m, o_jx, o_jy, o_jz);
+        else
+            collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, o_m, o_jx, o_jy, o_jz);
+        const long long cell = ((long long)z * ny + y) * nx + x;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Io<T>::st(dst + (size_t)q * N + cell, h[q]);
+    }
+
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    // last rotor CTA of this lattice: actuator line of the next step
+    if (rotor_tile) {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(D->rotor_counter, 1u);
+            s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_flag) {
+            __threadfence();
+            alm_compute<T>(D, dst, step + 1);
+            if (tid == 0) *D->rotor_counter = 0u;
+        }
+    }
+    // diagnostic step (uniform over the grid): FP64 sums, closed by the last CTA
+    if (diag) {
+        double v[4] = {o_m, o_jx, o_jy, o_jz};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_red[tid >> 5][k] = v[k];
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 0; k < 4; ++k) {
+                double sum = 0.0;
+                for (int w = 0; w < (nthreads >> 5); ++w) sum += s_red[w][k];
+                atomicAdd(D->diag_acc + k, sum);
+            }
+            __threadfence();
+            const unsigned prev = atomicAdd(A.diag_done, 1u);
+            if (prev == A.n_tiles - 1u) {
+                __threadfence();
+                for (int i = 0; i < A.n_inst; ++i) {
+                    const DevDomain* Di = A.dom + i;
+                    {
+                        bool finite = true;
+                        for (int k = 0; k < 4; ++k) {
+                            const double sum = __ldcg(Di->diag_acc + k);
+                            Di->diag_res[k] = sum;
+                            Di->diag_acc[k] = 0.0;
+                            if (!isfinite(sum)) finite = false;
+                        }
+                        Di->diag_res[4] = (double)step;
+                        if (!finite) atomicOr(Di->err, ERR_NONFINITE);
+                    }
+                }
+                *A.diag_done = 0u;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_alm(const DevDomain* dom, int parity, long long step)
+{
+    const DevDomain* D = dom + blockIdx.x;
+    if (D->n_el > 0) alm_compute<T>(D, (const T*)D->f[parity], step);
+}
+
+// f = feq(1 + drho, u) + fneq as offsets.  u = nullptr: the mean inflow profile
+// when inflow_mean, else 0.
+template <typename T>
+__global__ void k_init(const DevDomain* D, const float* drho, const float* u, const float* fneq, int parity,
+                       int inflow_mean)
+{
+    const long long N = D->N;
+    T* dst = (T*)D->f[parity];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+        if (u) {
+            ux = u[i];
+            uy = u[N + i];
+            uz = u[2 * N + i];
+        } else if (inflow_mean) {
+            const int z = (int)(i / ((long long)D->nx * D->ny));
+            double scale = 1.0;
+            if (D->inflow_kind == 1) scale = log((z + 0.5) / D->z0) * D->inv_log_zref_z0;
+            ux = (float)(D->u_ref[0] * scale);
+            uy = (float)(D->u_ref[1] * scale);
+            uz = (float)(D->u_ref[2] * scale);
+        }
+        float E[27];
+        feq_offsets(drho ? drho[i] : 0.0f, ux, uy, uz, E);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            float v = E[q];
+            if (fneq) v += fneq[(size_t)q * N + i];
+            Io<T>::st(dst + (size_t)q * N + i, v);
+        }
+    }
+}
+
+// rho = sum f*, u = (sum c f* - F/2)/rho with F the force of the last collision.
+template <typename T>
+__global__ void k_moments(const DevDomain* D, int parity, double* rho, double* u)
+{
+    const long long N = D->N;
+    const T* f = (const T*)D->f[parity];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float h[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldcg(f + (size_t)q * N + i);
+        const Moments M = raw_moments(h);
+        const int x = (int)(i % D->nx);
+        const int y = (int)((i / D->nx) % D->ny);
+        const int z = (int)(i / ((long long)D->nx * D->ny));
+        float F[3] = {D->body[0], D->body[1], D->body[2]};
+        alm_box_force(D, x, y, z, F);
+        const double r = 1.0 + (double)M.drho;
+        rho[i] = r;
+        u[i] = ((double)M.jx - 0.5 * (double)F[0]) / r;
+        u[N + i] = ((double)M.jy - 0.5 * (double)F[1]) / r;
+        u[2 * N + i] = ((double)M.jz - 0.5 * (double)F[2]) / r;
+    }
+}
+
+template <typename T>
+__global__ void k_to_float(const T* src, float* dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = Io<T>::ldcg(src + i);
+}
+
+template <typename T>
+__global__ void k_from_float(const float* src, T* dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Io<T>::st(dst + i, src[i]);
+}
+
+// ------------------------------------------------------------------ launchers
+
+static int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    const long long cap = 152LL * 16;
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a)
+{
+#define LBM_STEP_CASE(C, S, T)                                      \
+    if (coll == C && store == S) {                                  \
+        k_step<C, T><<<grid, block, 0, s>>>(a);                     \
+        return cudaGetLastError();                                  \
+    }
+    LBM_STEP_CASE(COLL_CUMULANT, STORE_FP32, float)
+    LBM_STEP_CASE(COLL_CUMULANT, STORE_BF16, __nv_bfloat16)
+    LBM_STEP_CASE(COLL_CUMULANT, STORE_FP16, __half)
+    LBM_STEP_CASE(COLL_SRT_SMAG, STORE_FP32, float)
+    LBM_STEP_CASE(COLL_SRT_SMAG, STORE_BF16, __nv_bfloat16)
+    LBM_STEP_CASE(COLL_SRT_SMAG, STORE_FP16, __half)
+#undef LBM_STEP_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s)
+{
+    if (store == STORE_FP32) k_alm<float><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
+    else if (store == STORE_BF16) k_alm<__nv_bfloat16><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
+    else k_alm<__half><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const float* drho, const float* u,
+                        const float* fneq, int parity, int inflow_mean, cudaStream_t s)
+{
+    const int g = grid_for(h.N, 256);
+    if (store == STORE_FP32) k_init<float><<<g, 256, 0, s>>>(d_dom_inst, drho, u, fneq, parity, inflow_mean);
+    else if (store == STORE_BF16) k_init<__nv_bfloat16><<<g, 256, 0, s>>>(d_dom_inst, drho, u, fneq, parity, inflow_mean);
+    else k_init<__half><<<g, 256, 0, s>>>(d_dom_inst, drho, u, fneq, parity, inflow_mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int store, const DevDomain* d_dom_inst, const DevDomain& h, int parity, double* rho,
+                           double* u, cudaStream_t s)
+{
+    const int g = grid_for(h.N, 256);
+    if (store == STORE_FP32) k_moments<float><<<g, 256, 0, s>>>(d_dom_inst, parity, rho, u);
+    else if (store == STORE_BF16) k_moments<__nv_bfloat16><<<g, 256, 0, s>>>(d_dom_inst, parity, rho, u);
+    else k_moments<__half><<<g, 256, 0, s>>>(d_dom_inst, parity, rho, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(int store, const void* src, float* dst, long long n, cudaStream_t s)
+{
+    const int g = grid_for(n, 256);
+    if (store == STORE_FP32) k_to_float<float><<<g, 256, 0, s>>>((const float*)src, dst, n);
+    else if (store == STORE_BF16) k_to_float<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16*)src, dst, n);
+    else k_to_float<__half><<<g, 256, 0, s>>>((const __half*)src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_float(int store, const float* src, void* dst, long long n, cudaStream_t s)
+{
+    const int g = grid_for(n, 256);
+    if (store == STORE_FP32) k_from_float<float><<<g, 256, 0, s>>>(src, (float*)dst, n);
+    else if (store == STORE_BF16) k_from_float<__nv_bfloat16><<<g, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n);
+    else k_from_float<__half><<<g, 256, 0, s>>>(src, (__half*)dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb

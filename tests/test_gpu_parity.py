@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: FP32 collision arithmetic on FP32 offsets f - w gives velocity
+errors of a few 1e-9 per step; the bound max|du| <= 1e-6 lattice units on
+laminar cases leaves room for a few hundred steps of accumulation.  PDFs are
+compared element by element after one step to 2e-7 (absolute, f ~ 0.3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2402_13171_gb300 import inputs as I
+from cases import max_du, setup_pair
+
+pytestmark = pytest.mark.gpu
+
+DU_TOL = 1e-6
+F_TOL = 2e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2402_13171_gb300 import build
+    build.build()
+    O.build()
+
+
+def test_taylor_green_32_cubed_200_steps():
+    """3-D Taylor-Green vortex, 32^3, u0 = 0.05, nu = 0.01, 200 steps, cumulant."""
+    dom = dict(nx=32, ny=32, nz=32, nu=0.01)
+    rho, u = I.taylor_green_3d(32, 0.05)
+    g, s = setup_pair(dom, rho=rho, u=u)
+    g.step(200)
+    s.step(200)
+    du = max_du(g, s)
+    print(f"TGV 32^3 200 steps: max|du| = {du:.3e}")
+    assert du <= DU_TOL
+    # kinetic energy follows the oracle's
+    rg, ug = g.moments()
+    ro, uo = s.moments()
+    Eg = 0.5 * np.sum(rg * (ug ** 2).sum(0))
+    Eo = 0.5 * np.sum(ro * (uo ** 2).sum(0))
+    # |dE|/E <~ 2 max|du| / u0 = 4e-5 at the velocity bound
+    assert Eg == pytest.approx(Eo, rel=4e-5)
+
+
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
+@pytest.mark.parametrize("shape", [(37, 19, 11), (5, 4, 3), (1, 1, 1), (130, 3, 2)])
+def test_one_step_pdfs_random_state(coll, shape):
+    """Seeded near-equilibrium state on ragged periodic lattices (tails of the
+    128-wide tiles, single cells): every post-collision PDF after one step."""
+    nx, ny, nz = shape
+    dom = dict(nx=nx, ny=ny, nz=nz, collision=coll, nu=0.02, smag_c=0.17, body_force=(1e-5, -2e-5, 3e-6))
+    rho, u, fneq = I.random_state(nx, ny, nz, seed=101 + nx)
+    g, s = setup_pair(dom, rho=rho, u=u, fneq=fneq)
+    np.testing.assert_allclose(g.pdfs(), s.f, atol=F_TOL, rtol=0)
+    g.step(1)
+    s.step(1)
+    np.testing.assert_allclose(g.pdfs(), s.f, atol=F_TOL, rtol=0)
+    g.step(4)
+    s.step(4)
+    assert max_du(g, s) <= DU_TOL
+
+
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
+def test_bounce_back_poiseuille(coll):
+    dom = dict(nx=3, ny=16, nz=2, collision=coll, nu=0.1, bc=("periodic", "noslip", "periodic"),
+               body_force=(1e-6, 0, 0))
+    g, s = setup_pair(dom)
+    g.step(300)
+    s.step(300)
+    assert max_du(g, s) <= DU_TOL
+    dom2 = dict(nx=7, ny=9, nz=6, collision=coll, nu=0.05, bc=("noslip", "noslip", "noslip"),
+                body_force=(1e-5, 5e-6, -3e-6))
+    rho, u, fneq = I.random_state(7, 9, 6, seed=7)
+    g, s = setup_pair(dom2, rho=rho, u=u, fneq=fneq)
+    g.step(1)
+    s.step(1)
+    np.testing.assert_allclose(g.pdfs(), s.f, atol=F_TOL, rtol=0)
+    g.step(20)
+    s.step(20)
+    assert max_du(g, s) <= DU_TOL
+
+
+def test_inlet_outlet_noise():
+    dom = dict(nx=40, ny=12, nz=9, nu=0.01, bc=("inout", "periodic", "periodic"), u_ref=(0.05, 0.0, 0.0),
+               noise_rel=0.01, seed=12345)
+    g, s = setup_pair(dom, inflow=True)
+    g.step(1)
+    s.step(1)
+    np.testing.assert_allclose(g.pdfs(), s.f, atol=F_TOL, rtol=0)
+    g.step(60)
+    s.step(60)
+    assert max_du(g, s) <= DU_TOL
+
+
+def small_rotor_case(collision="cumulant"):
+    dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777)
+    dom["collision"] = collision
+    return dom, turb
+
+
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
+def test_rotor_short_horizon(coll):
+    """Actuator line + inlet/outlet + noise on a scaled-down single-rotor case:
+    flow, element forces and FP64 rotor loads stay with the oracle."""
+    dom, turb = small_rotor_case(coll)
+    g, s = setup_pair(dom, [turb], inflow=True)
+    for n in (1, 10, 50):
+        g.step(n - s.step_count)
+        s.step(n - s.step_count)
+        du = max_du(g, s)
+        th, tq, ef, ep = g.loads(0, elements=True)
+        print(f"{coll} step {n}: max|du| {du:.2e}  thrust {th:.6e} vs {s.loads[0, 0]:.6e}")
+        assert du <= DU_TOL
+        np.testing.assert_allclose(ep, s.elem_pos, atol=2e-5)
+        # element forces scale with |u_rel|^2: relative error ~ 2 max|du| / |u_rel| <= 2e-6 / 0.05
+        np.testing.assert_allclose(ef, s.elem_force, atol=1e-7 + 5e-5 * np.abs(s.elem_force).max())
+        assert th == pytest.approx(s.loads[0, 0], rel=5e-5)
+        assert tq == pytest.approx(s.loads[0, 1], rel=5e-5)
+
+
+def test_rotor_force_sum_matches_blade_forces():
+    """One step of momentum change equals minus the applied blade forces."""
+    dom, turb = small_rotor_case()
+    dom["bc"] = ("periodic", "periodic", "periodic")
+    g, s = setup_pair(dom, [turb], u=np.stack([np.full((40, 40, 64), 0.05), np.zeros((40, 40, 64)),
+                                               np.zeros((40, 40, 64))]))
+    C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
+    j0 = np.einsum("qa,qzyx->a", C, g.pdfs())
+    _, _, ef0, _ = g.loads(0, elements=True)  # forces of step 0
+    g.step(1)
+    j1 = np.einsum("qa,qzyx->a", C, g.pdfs())
+    # FP32 storage of ~1e5 cells rounds the summed momentum at the 1e-5 relative level
+    np.testing.assert_allclose(j1 - j0, -ef0.astype(np.float64).sum(0), rtol=2e-5, atol=1e-7)
+
+
+def test_full_size_single_turbine_sampled():
+    """256x128x128 single-rotor workload in the launch configuration of the
+    benchmark: one step from a seeded state, checked at sampled cells (rotor
+    box, inlet, outlet, bulk) and on every element force, against the
+    oracle's per-cell update."""
+    dom, turb = I.single_turbine_case()
+    nx, ny, nz = dom["nx"], dom["ny"], dom["nz"]
+    rho, u, fneq = I.random_state(nx, ny, nz, seed=4242, u_mean=(0.05, 0, 0), du=0.005, drho=0.002, fneq_amp=2e-4)
+    g, s = setup_pair(dom, [turb], rho=rho, u=u, fneq=fneq, inflow=True)
+    f0 = s.f.copy()
+    # oracle: element forces of step 0 and the spread force at sampled cells
+    pos, fb, alpha, loads = s.alm_forces(f0, np.zeros((3, nz, ny, nx)), 0)
+    th, tq, ef, ep = g.loads(0, elements=True)
+    np.testing.assert_allclose(ep, pos, atol=2e-5)
+    np.testing.assert_allclose(ef, fb, atol=1e-5 * np.abs(fb).max())
+    assert th == pytest.approx(loads[0], rel=1e-5)
+    g.step(1)
+    fg = g.pdfs()
+    rng = np.random.default_rng(9)
+    cells = [(0, 5, 7), (255, 127, 0), (64, 64, 64), (60, 50, 70), (70, 80, 48), (1, 0, 127), (254, 64, 3)]
+    cells += [tuple(int(v) for v in c) for c in rng.integers([52, 42, 42], [76, 86, 86], (12, 3))]
+    cells += [tuple(int(v) for v in c) for c in rng.integers([0, 0, 0], [256, 128, 128], (12, 3))]
+    eps = turb["epsilon"]
+    for (x, y, z) in cells:
+        F = O.spread_at(pos, fb, eps, x, y, z)
+        ref = s.update_cell(f0, F, 0, x, y, z)
+        np.testing.assert_allclose(fg[:, z, y, x], ref, atol=F_TOL, rtol=0, err_msg=str((x, y, z)))
+
+
+@pytest.mark.parametrize("tile", [(32, 4), (64, 2), (256, 1), (96, 1)])
+def test_tile_shapes_agree(tile):
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    gb, _ = setup_pair(dom, [turb], inflow=True, tile=tile)
+    ga.step(7)
+    gb.step(7)
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+
+
+def test_graph_replay_equals_direct_launches():
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    gb, _ = setup_pair(dom, [turb], inflow=True)
+    gb.set_profiling(True)
+    ga.step(9)
+    gb.step(9)
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    ms, n = gb.kernel_time()
+    assert n == 9 and ms > 0
+
+
+def test_checkpoint_resume_is_bitwise():
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    ga.step(11)
+    f = ga.pdfs()
+    n = ga.step_count()
+    ga.step(6)
+    gb, _ = setup_pair(dom, [turb], inflow=True)
+    gb.step(3)          # different history, then restore
+    gb.set_pdfs(f)
+    gb.set_step(n)
+    gb.step(6)
+    # the lagged ALM force is not part of the PDFs: compare flow away from the rotor box
+    # and the loads after the restart transient
+    fa, fb = ga.pdfs(), gb.pdfs()
+    assert np.abs(fa - fb).max() < 1e-4
+    dom2 = dict(nx=20, ny=10, nz=6, nu=0.02, bc=("inout", "periodic", "periodic"), u_ref=(0.04, 0, 0),
+                noise_rel=0.01, seed=5)
+    ha, _ = setup_pair(dom2, inflow=True)
+    ha.step(13)
+    f = ha.pdfs()
+    ha.step(5)
+    hb, _ = setup_pair(dom2, inflow=True)
+    hb.set_pdfs(f)
+    hb.set_step(13)
+    hb.step(5)
+    np.testing.assert_array_equal(ha.pdfs(), hb.pdfs())
+
+
+def test_diagnostics_fp64_sums():
+    dom = dict(nx=33, ny=17, nz=9, nu=0.02, body_force=(1e-5, 0, 0))
+    rho, u, fneq = I.random_state(33, 17, 9, seed=3)
+    g, s = setup_pair(dom, rho=rho, u=u, fneq=fneq, diag_every=5)
+    g.step(11)  # diagnostic steps 0, 5, 10
+    mm, at = g.diagnostics()
+    assert at == 10
+    g2, _ = setup_pair(dom, rho=rho, u=u, fneq=fneq)
+    g2.step(11)
+    f = g2.pdfs()
+    C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
+    # sums of the offsets: mass - N, momentum
+    assert mm[0] == pytest.approx((f.sum() - f[0].size), abs=1e-6)
+    np.testing.assert_allclose(mm[1:], np.einsum("qa,qzyx->a", C, f), atol=1e-6)
+
+
+def test_batch_equals_separate_runs():
+    from paper_2402_13171_gb300 import lbm
+    dom1, t1 = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=1)
+    dom2, t2 = I.single_turbine_case(72, 48, 44, diameter=20.0, elements_per_blade=6, seed=2, tsr=4.0, u_inf=0.04)
+    dom3 = dict(nx=33, ny=17, nz=9, nu=0.02, body_force=(1e-5, 0, 0))
+    cfgs = []
+    for d in (dom1, dom2, dom3):
+        cfgs.append(dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], collision="cumulant", nu=d["nu"],
+                         bc=d.get("bc", ("periodic",) * 3), body_force=d.get("body_force", (0, 0, 0)),
+                         seed=d.get("seed", 0)))
+    lat = lbm.batch_create(cfgs)
+    singles = []
+    for d, t, L in ((dom1, t1, lat[0]), (dom2, t2, lat[1]), (dom3, None, lat[2])):
+        gs, _ = setup_pair(d, [t] if t else [], inflow="u_ref" in d)
+        singles.append(gs)
+        if "u_ref" in d:
+            L.set_inflow(u_ref=d["u_ref"], noise_rel=d["noise_rel"])
+        if t:
+            L.add_turbine(**t)
+        if "u_ref" not in d:
+            L.init_fields()
+    lat[0].step(12)
+    for gs in singles:
+        gs.step(12)
+    for L, gs in zip(lat, singles):
+        np.testing.assert_array_equal(L.pdfs(), gs.pdfs())
+    assert lat[0].loads(0) == singles[0].loads(0)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+def test_sixteen_bit_storage_tracks_fp32(storage):
+    dom = dict(nx=32, ny=32, nz=32, nu=0.01)
+    rho, u = I.taylor_green_3d(32, 0.05)
+    g32, s = setup_pair(dom, rho=rho, u=u)
+    g16, _ = setup_pair(dom, rho=rho, u=u, storage=storage)
+    g32.step(100)
+    g16.step(100)
+    s.step(100)
+    _, u32 = g32.moments()
+    _, u16 = g16.moments()
+    _, uo = s.moments()
+    err = np.abs(u16 - uo).max()
+    print(f"{storage}: max|du| vs oracle {err:.3e}, fp32 {np.abs(u32 - uo).max():.3e}")
+    # 8-bit (bf16) / 11-bit (fp16) mantissas on offsets of ~0.05: per-step rounding 2e-4 / 2.5e-5
+    assert err < (1e-3 if storage == "bf16" else 1e-4)
