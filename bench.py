@@ -38,7 +38,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32")
     p.add_argument("--collision", choices=["cumulant", "srt_smag"], default="cumulant")
-    p.add_argument("--tile", type=str, default="128x1")
+    p.add_argument("--tile", type=str, default="32x4")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()

@@ -77,7 +77,8 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* user); /* optional device allocator */
     void (*dev_free)(void* ptr, void* user);
     void* alloc_user;
-    int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 128 x 1 */
+    int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 32 x 4;
+                                tile_x a multiple of 32, tile_x * tile_y <= 256 */
 } lbm_config;
 
 typedef struct {

@@ -47,7 +47,7 @@ struct Batch {
     unsigned int* d_diag_done = nullptr;
     int diag_every = 0;
     long long host_step = 0;
-    int tile_x = 128, tile_y = 1;
+    int tile_x = 32, tile_y = 4;
     lbm_status status = LBM_OK;
     std::string err;
     bool dirty = true;
@@ -136,7 +136,10 @@ lbm_status validate_cfg(const lbm_config* c, std::string& msg)
         msg = "lattice sizes must be in [1, 65535]";
         return LBM_ERR_INVALID_ARG;
     }
-    if ((long long)c->nx * c->ny * c->nz * 27LL >= (1LL << 40)) { msg = "lattice too large"; return LBM_ERR_INVALID_ARG; }
+    if ((long long)c->nx * c->ny * c->nz * 27LL >= (1LL << 31)) {
+        msg = "lattice too large: 27 * nx * ny * nz must stay below 2^31 (79,536,431 cells)";
+        return LBM_ERR_INVALID_ARG;
+    }
     if (c->collision != LBM_COLL_CUMULANT && c->collision != LBM_COLL_SRT_SMAGORINSKY) {
         msg = "unknown collision";
         return LBM_ERR_INVALID_ARG;
@@ -149,7 +152,7 @@ lbm_status validate_cfg(const lbm_config* c, std::string& msg)
     }
     if (c->bc[0] == LBM_BC_INFLOW_OUTFLOW && c->nx < 2) { msg = "inflow/outflow needs nx >= 2"; return LBM_ERR_INVALID_ARG; }
     if (c->diag_every < 0) { msg = "diag_every must be >= 0"; return LBM_ERR_INVALID_ARG; }
-    const int tx = c->tile_x ? c->tile_x : 128, ty = c->tile_y ? c->tile_y : 1;
+    const int tx = c->tile_x ? c->tile_x : 32, ty = c->tile_y ? c->tile_y : 4;
     if (tx < 32 || tx % 32 != 0 || ty < 1 || tx * ty > 256) {
         msg = "tile_x must be a multiple of 32 and tile_x * tile_y <= 256";
         return LBM_ERR_INVALID_ARG;
@@ -177,7 +180,25 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
     h.z0 = 0.1;
     h.inv_log_zref_z0 = 1.0;
     h.noise_amp = 0.0;
+    h.noise_amp_f = 0.0f;
+    h.u_ref_f[0] = h.u_ref_f[1] = h.u_ref_f[2] = 0.0f;
     h.seed = c.seed;
+    h.inflow_scale = (float*)dalloc(b, sizeof(float) * c.nz);
+    if (!h.inflow_scale) return fail(b, LBM_ERR_OOM, "inflow table allocation failed");
+    {
+        std::vector<float> ones(c.nz, 1.0f);
+        CK(cudaMemcpyAsync(h.inflow_scale, ones.data(), sizeof(float) * c.nz, cudaMemcpyHostToDevice, b->stream));
+        if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    }
+    h.inflow_u[0] = h.inflow_u[1] = nullptr;
+    if (c.bc[0] == LBM_BC_INFLOW_OUTFLOW) {
+        const size_t ib = sizeof(float) * 3 * (size_t)c.ny * c.nz;
+        float* u2 = (float*)dalloc(b, 2 * ib);
+        if (!u2) return fail(b, LBM_ERR_OOM, "inflow buffer allocation failed");
+        CK(cudaMemsetAsync(u2, 0, 2 * ib, b->stream));
+        h.inflow_u[0] = u2;
+        h.inflow_u[1] = u2 + 3 * (size_t)c.ny * c.nz;
+    }
     const size_t fbytes = (size_t)h.N * 27 * store_bytes(b->store);
     for (int p = 0; p < 2; ++p) {
         h.f[p] = dalloc(b, fbytes);
@@ -288,11 +309,14 @@ lbm_status launch_one(Batch* b, int parity)
     return LBM_OK;
 }
 
-// Actuator line of the current step for every lattice (after a state change).
+// Inlet velocities and actuator line of the current step for every lattice
+// (after a state change).
 lbm_status refresh_alm(Batch* b)
 {
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (b->inst[i].h.bc[0] == BC_INOUT) CK(launch_inflow(b->d_dom + i, b->inst[i].h, b->host_step, b->stream));
     bool any = false;
     for (auto& I : b->inst) any = any || I.h.n_el > 0;
     if (!any) return LBM_OK;
@@ -337,8 +361,8 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     b->ualloc = cfgs[0].dev_alloc;
     b->ufree = cfgs[0].dev_free;
     b->user = cfgs[0].alloc_user;
-    b->tile_x = cfgs[0].tile_x ? cfgs[0].tile_x : 128;
-    b->tile_y = cfgs[0].tile_y ? cfgs[0].tile_y : 1;
+    b->tile_x = cfgs[0].tile_x ? cfgs[0].tile_x : 32;
+    b->tile_y = cfgs[0].tile_y ? cfgs[0].tile_y : 4;
     b->diag_every = cfgs[0].diag_every;
     b->inst.resize(n);
     lbm_status s = LBM_OK;
@@ -430,6 +454,15 @@ lbm_status lbm_set_inflow(lbm_ctx* ctx, const lbm_inflow* in)
     I.h.inv_log_zref_z0 = in->kind == 1 ? 1.0 / std::log(in->z_ref / in->z0) : 1.0;
     const double U0 = std::sqrt(in->u_ref[0] * in->u_ref[0] + in->u_ref[1] * in->u_ref[1] + in->u_ref[2] * in->u_ref[2]);
     I.h.noise_amp = in->noise_rel * U0;
+    I.h.noise_amp_f = (float)I.h.noise_amp;
+    for (int a = 0; a < 3; ++a) I.h.u_ref_f[a] = (float)in->u_ref[a];
+    {
+        std::vector<float> sc(I.h.nz, 1.0f);
+        if (in->kind == 1)
+            for (int z = 0; z < I.h.nz; ++z) sc[z] = (float)(std::log((z + 0.5) / in->z0) / std::log(in->z_ref / in->z0));
+        CK(cudaMemcpyAsync(I.h.inflow_scale, sc.data(), sizeof(float) * I.h.nz, cudaMemcpyHostToDevice, b->stream));
+        if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    }
     b->dirty = true;
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;

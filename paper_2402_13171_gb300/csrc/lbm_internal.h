@@ -57,6 +57,9 @@ struct DevDomain {
     double z0, inv_log_zref_z0;
     double noise_amp;          // noise_rel * |u_ref|
     unsigned long long seed;
+    float u_ref_f[3], noise_amp_f;
+    float* inflow_scale;       // nz: mean-profile factor per z plane (1, or the log law)
+    float* inflow_u[2];        // by step parity: inlet velocity per column, [3][nz][ny] (x inlet only)
     void* f[2];                // PDF offset arrays [27][nz][ny][nx] of the storage type
     int n_turb;
     DevTurbine* turb;          // device array of n_turb
@@ -97,6 +100,7 @@ __host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0,
 // Host-side launchers (lbm_kernels.cu).
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a);
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
+cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);
 cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const float* drho,
                         const float* u, const float* fneq, int parity, int inflow_mean, cudaStream_t s);
 cudaError_t launch_moments(int store, const DevDomain* d_dom_inst, const DevDomain& h, int parity, double* rho,

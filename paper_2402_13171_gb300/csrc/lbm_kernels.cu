@@ -55,19 +55,22 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
     return z ^ (z >> 31);
 }
 
-// Inflow velocity of inlet column (y, z) at step n: mean profile + per-component
-// noise noise_amp * xi, xi in [-1, 1) from the top 53 bits; FP64, rounded to FP32.
-__device__ void inflow_velocity(const DevDomain* D, long long step, int y, int z, float u[3])
+// Inflow velocity of inlet column (y, z) at step n: mean profile u_ref * scale(z)
+// plus, per component a, noise_amp * xi with xi = (r >> 11) 2^-53 * 2 - 1 from
+// the splitmix64 output r for counter ((n nz + z) ny + y) 3 + a + 1.  In FP32
+// only the top 24 of those 53 bits are kept (converted exactly), which moves xi
+// by less than 2^-23, one FP32 ulp of xi.
+__device__ __forceinline__ void inflow_velocity(const DevDomain* D, long long step, int y, int z, float u[3])
 {
-    double scale = 1.0;
-    if (D->inflow_kind == 1) scale = log((z + 0.5) / D->z0) * D->inv_log_zref_z0;
+    const float scale = D->inflow_scale[z];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        unsigned long long counter =
+        const unsigned long long counter =
             (((unsigned long long)step * (unsigned long long)D->nz + (unsigned long long)z) * (unsigned long long)D->ny +
              (unsigned long long)y) * 3ull + (unsigned long long)a;
-        unsigned long long r = splitmix64(D->seed, counter + 1ull);
-        double xi = (double)(r >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
-        u[a] = (float)(D->u_ref[a] * scale + D->noise_amp * xi);
+        const unsigned long long r = splitmix64(D->seed, counter + 1ull);
+        const float xi = (float)(unsigned)(r >> 40) * 0x1p-23f - 1.0f;
+        u[a] = fmaf(D->noise_amp_f, xi, D->u_ref_f[a] * scale);
     }
 }
 
@@ -316,38 +319,29 @@ __device__ __forceinline__ long long cell_of(const DevDomain* D, int x, int y, i
     return ((long long)z * D->ny + y) * D->nx + x;
 }
 
-// Pre-collision population q of cell (x, y, z) by the general boundary rules:
-// no-slip (halfway bounce-back) first, then periodic wrap, then the x inlet
-// (equilibrium at rho = 1 and the inflow velocity of the source column) and
-// outlet (source moved to the last plane).
-template <typename T, bool CG>
-__device__ float pull_general(const DevDomain* D, const T* f, int q, int x, int y, int z, long long step)
+// Halfway bounce-back for a cell next to a no-slip face, applied after the
+// clamped loads of k_step (out of line: wall cells are few): every direction q
+// whose source x - c_q lies outside the lattice along a no-slip axis takes the
+// cell's own post-collision population of the opposite direction.  Wall rules
+// take precedence over the x inlet, whose values were patched before.
+template <typename T>
+__device__ __noinline__ void boundary_patch(const DevDomain* D, const T* src, int x, int y, int z, long long step,
+                                            float* h)
 {
-    const int c[3] = {qcx(q), qcy(q), qcz(q)};
     const int n[3] = {D->nx, D->ny, D->nz};
-    int s[3] = {x - c[0], y - c[1], z - c[2]};
-    bool wall = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (D->bc[a] == BC_NOSLIP && (s[a] < 0 || s[a] >= n[a])) wall = true;
-    const T* p;
-    if (wall) {
-        p = f + (size_t)(26 - q) * D->N + cell_of(D, x, y, z);
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (D->bc[a] == BC_PERIODIC) s[a] = s[a] < 0 ? s[a] + n[a] : (s[a] >= n[a] ? s[a] - n[a] : s[a]);
-        if (D->bc[0] == BC_INOUT) {
-            if (s[0] < 0) {
-                float u[3];
-                inflow_velocity(D, step, s[1], s[2], u);
-                return feq_offset_one(q, u[0], u[1], u[2]);
-            }
-            if (s[0] >= n[0]) s[0] = n[0] - 1;
+    const int p[3] = {x, y, z};
+    const unsigned cell = (unsigned)(((long long)z * D->ny + y) * D->nx + x);
+    const unsigned N = (unsigned)D->N;
+    (void)step;
+    for (int q = 0; q < 27; ++q) {
+        const int c[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+        bool wall = false;
+        for (int a = 0; a < 3; ++a) {
+            const int s = p[a] - c[a];
+            if (D->bc[a] == BC_NOSLIP && (s < 0 || s >= n[a])) wall = true;
         }
-        p = f + (size_t)q * D->N + cell_of(D, s[0], s[1], s[2]);
+        if (wall) h[q] = Io<T>::ld(src + (unsigned)(26 - q) * N + cell);
     }
-    return CG ? Io<T>::ldcg(p) : Io<T>::ld(p);
 }
 
 // ------------------------------------------------------------------ actuator line
@@ -585,8 +579,12 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
 template <int COLL, typename T>
 __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
 {
+    constexpr int kCull = 128;  // blade elements kept per rotor tile
     __shared__ double s_red[8][4];
     __shared__ int s_flag;
+    __shared__ float4 s_pos[kCull], s_frc[kCull];
+    __shared__ int s_tag[kCull];
+    __shared__ int s_cnt[8];
     const unsigned long long tile = A.tiles[blockIdx.x];
     const bool rotor_tile = (tile >> 63) != 0;
     const int inst = (int)((tile >> 48) & 0x7FFF);
@@ -602,32 +600,116 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
     T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
     const bool diag = A.diag_every > 0 && (step % A.diag_every) == 0;  // uniform over the grid
     float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+
+    // rotor tile: keep the blade elements whose support reaches the tile, in
+    // element order (n_cull = -1: too many, every cell scans all elements)
+    int n_cull = -1;
+    if (rotor_tile) {
+        const float tx0 = (float)(tile & 0xFFFF), ty0 = (float)((tile >> 16) & 0xFFFF);
+        const float tx1 = tx0 + (float)(blockDim.x - 1), ty1 = ty0 + (float)(blockDim.y - 1);
+        const float4* P = D->el_pos[step & 1];
+        const float4* Fe = D->el_force[step & 1];
+        const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
+        int total = 0;
+        for (int base = 0; base < D->n_el; base += nthreads) {
+            const int e = base + tid;
+            bool keep = false;
+            float4 pe = make_float4(0.f, 0.f, 0.f, 0.f);
+            int t = 0;
+            if (e < D->n_el) {
+                pe = __ldg(P + e);
+                while (t + 1 < D->n_turb && D->turb[t + 1].el_offset <= e) ++t;
+                const float cut = D->turb[t].cut;
+                keep = pe.x + cut >= tx0 && pe.x - cut <= tx1 && pe.y + cut >= ty0 && pe.y - cut <= ty1 &&
+                       fabsf(pe.z - (float)z) <= cut;
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+            if (lane == 0) s_cnt[warp] = __popc(m);
+            __syncthreads();
+            int off = total, chunk = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                if (w < warp) off += s_cnt[w];
+                chunk += s_cnt[w];
+            }
+            const int pos = off + __popc(m & ((1u << lane) - 1u));
+            if (keep && pos < kCull) {
+                s_pos[pos] = pe;
+                s_frc[pos] = __ldg(Fe + e);
+                s_tag[pos] = t;
+            }
+            total += chunk;
+            __syncthreads();
+        }
+        n_cull = total <= kCull ? total : -1;
+    }
 
     if (x < nx && y < ny) {
         float h[27];
-        // neighbour coordinates and the fast/special decision
-        bool special = false;
-        int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+        // source coordinates for c = +1 (m) and c = -1 (p): wrapped on periodic
+        // axes, clamped otherwise (the outlet rule; other faces are patched below)
         const int bx = D->bc[0], by = D->bc[1], bz = D->bc[2];
+        int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
         if (bx == BC_PERIODIC) { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
-        else if (bx == BC_INOUT) { if (xm < 0) special = true; if (xp >= nx) xp = nx - 1; }
-        else { if (xm < 0 || xp >= nx) special = true; }
+        else { xm = max(xm, 0); xp = min(xp, nx - 1); }
         if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
-        else if (ym < 0 || yp >= ny) special = true;
+        else { ym = max(ym, 0); yp = min(yp, ny - 1); }
         if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
-        else if (zm < 0 || zp >= nz) special = true;
-        if (!special) {
-            const int xs[3] = {xp, x, xm};  // source x for cx = -1, 0, +1
-            const int ys[3] = {yp, y, ym};
-            const int zs[3] = {zp, z, zm};
+        else { zm = max(zm, 0); zp = min(zp, nz - 1); }
+        const bool walls = (bx == BC_NOSLIP && (x == 0 || x == nx - 1)) || (by == BC_NOSLIP && (y == 0 || y == ny - 1)) ||
+                           (bz == BC_NOSLIP && (z == 0 || z == nz - 1));
+        // 32-bit offsets: 27 N < 2^31 is checked on the host
+        const unsigned uN = (unsigned)N;
+        const unsigned xs[3] = {(unsigned)xp, (unsigned)x, (unsigned)xm};  // source x for cx = -1, 0, +1
+        const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+        const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
 #pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const long long sc = ((long long)zs[q / 9] * ny + ys[(q / 3) % 3]) * nx + xs[q % 3];
-                h[q] = Io<T>::ld(src + (size_t)q * N + sc);
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const unsigned row = (zs[k] * (unsigned)ny + ys[j]) * (unsigned)nx;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int q = k * 9 + j * 3 + i;
+                    h[q] = Io<T>::ld(src + ((unsigned)q * uN + row + xs[i]));
+                }
             }
-        } else {
+        // x inlet: the nine directions with c_x = +1 come from the ghost column
+        // (y - c_y, z - c_z): equilibrium at rho = 1 and that column's inlet velocity
+        if (bx == BC_INOUT && x == 0) {
+            const float* ub = D->inflow_u[step & 1];
+            const int plane = ny * nz;
 #pragma unroll
-            for (int q = 0; q < 27; ++q) h[q] = pull_general<T, false>(D, src, q, x, y, z, step);
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int q = k * 9 + j * 3 + 2;
+                    const bool wall = (by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
+                                      (bz == BC_NOSLIP && ((k == 2 && z == 0) || (k == 0 && z == nz - 1)));
+                    if (!wall) {
+                        const int col = (int)zs[k] * ny + (int)ys[j];
+                        h[q] = feq_offset_one(q, ub[col], ub[plane + col], ub[2 * plane + col]);
+                    }
+                }
+        }
+        if (walls) {
+            float hl[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) hl[q] = h[q];
+            boundary_patch<T>(D, src, x, y, z, step, hl);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) h[q] = hl[q];
+        }
+        // the x = 0 lane of each row prepares the inlet velocity of its column for step n+1
+        if (bx == BC_INOUT && x == 0) {
+            float u[3];
+            inflow_velocity(D, step + 1, y, z, u);
+            float* ub = D->inflow_u[(step + 1) & 1];
+            const int plane = ny * nz, col = z * ny + y;
+            ub[col] = u[0];
+            ub[plane + col] = u[1];
+            ub[2 * plane + col] = u[2];
         }
         // force: body + regularised blade forces inside the rotor boxes
         float F[3] = {D->body[0], D->body[1], D->body[2]};
@@ -641,15 +723,30 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
                 const int ne = B->n_blades * B->n_elements;
                 const float cut = B->cut, ie2 = B->inv_eps2;
                 float ax = 0.0f, ay = 0.0f, az = 0.0f;
-                for (int e = 0; e < ne; ++e) {
-                    const float4 pe = __ldg(P + B->el_offset + e);
-                    const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
-                    if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
-                        const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
-                        const float4 fe = __ldg(Fe + B->el_offset + e);
-                        ax -= w * fe.x;
-                        ay -= w * fe.y;
-                        az -= w * fe.z;
+                if (n_cull >= 0) {
+                    for (int i = 0; i < n_cull; ++i) {
+                        if (s_tag[i] != t) continue;
+                        const float4 pe = s_pos[i];
+                        const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
+                        if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
+                            const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
+                            const float4 fe = s_frc[i];
+                            ax -= w * fe.x;
+                            ay -= w * fe.y;
+                            az -= w * fe.z;
+                        }
+                    }
+                } else {
+                    for (int e = 0; e < ne; ++e) {
+                        const float4 pe = __ldg(P + B->el_offset + e);
+                        const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
+                        if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
+                            const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
+                            const float4 fe = __ldg(Fe + B->el_offset + e);
+                            ax -= w * fe.x;
+                            ay -= w * fe.y;
+                            az -= w * fe.z;
+                        }
                     }
                 }
                 const long long bi = ((long long)(z - B->lo[2]) * B->bny + (y - B->lo[1])) * B->bnx + (x - B->lo[0]);
@@ -665,13 +762,11 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
             collide_cumulant(h, F[0], F[1], F[2], D->omega, o_m, o_jx, o_jy, o_jz);
         else
             collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, o_m, o_jx, o_jy, o_jz);
-        const long long cell = ((long long)z * ny + y) * nx + x;
+        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
 #pragma unroll
-        for (int q = 0; q < 27; ++q) Io<T>::st(dst + (size_t)q * N + cell, h[q]);
+        for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
     }
 
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthreads = blockDim.x * blockDim.y;
     // last rotor CTA of this lattice: actuator line of the next step
     if (rotor_tile) {
         __syncthreads();
@@ -733,6 +828,20 @@ __global__ void k_alm(const DevDomain* dom, int parity, long long step)
 {
     const DevDomain* D = dom + blockIdx.x;
     if (D->n_el > 0) alm_compute<T>(D, (const T*)D->f[parity], step);
+}
+
+// Inlet velocities of every column for step `step` (after a state change).
+__global__ void k_inflow(const DevDomain* D, long long step)
+{
+    const int plane = D->ny * D->nz;
+    float* ub = D->inflow_u[step & 1];
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < plane; col += gridDim.x * blockDim.x) {
+        float u[3];
+        inflow_velocity(D, step, col % D->ny, col / D->ny, u);
+        ub[col] = u[0];
+        ub[plane + col] = u[1];
+        ub[2 * plane + col] = u[2];
+    }
 }
 
 // f = feq(1 + drho, u) + fneq as offsets.  u = nullptr: the mean inflow profile
@@ -837,6 +946,12 @@ cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity
     if (store == STORE_FP32) k_alm<float><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
     else if (store == STORE_BF16) k_alm<__nv_bfloat16><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
     else k_alm<__half><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s)
+{
+    k_inflow<<<grid_for((long long)h.ny * h.nz, 256), 256, 0, s>>>(d_dom_inst, step);
     return cudaGetLastError();
 }
 
