@@ -184,6 +184,31 @@ lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launche
  * stores of the storage type) and the number of cells of one launch. */
 lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_launch);
 
+/* Actuator-line evaluation for callers that cannot allocate device memory:
+ * a real-time turbine-controller loop, or code embedded in another framework
+ * that owns the memory pool, where cudaMalloc/cudaFree may synchronise the
+ * device, take unbounded time or be forbidden.  The paper has no counterpart.
+ * It is the same evaluation as a lattice's actuator line (kinematics,
+ * trilinear sampling, blade-element forces, FP64 thrust and torque) for one
+ * rotor at step `step` on a caller-owned field, with no lagged blade force
+ * (only body_force enters the half-force shift of the sampled velocity).
+ *   pdf_offsets  device, FP32 offsets f - w, [27][nz][ny][nx]; 27*nx*ny*nz < 2^31
+ *   desc         as for alm_add_turbine; its support must lie inside [1, n-2]
+ *   elem_force   device, 3 floats per element (blade-major): blade forces
+ *   elem_pos     device, 3 floats per element, or NULL
+ *   loads        device, 2 doubles: thrust, torque
+ * Work is enqueued on cuda_stream (NULL = legacy default stream); the call
+ * returns without waiting.  Nothing is allocated: the scratch is one static
+ * device block of about 300 KB that every GPU loading this library holds
+ * until the process exits.  Limits: at most 1024 elements and 8192 polar
+ * points (INVALID_ARG beyond, before anything is enqueued).  The first call
+ * on a device looks up the block's address (make it before any stream
+ * capture).  All calls share the block: calls that overlap on the GPU race.
+ * Errors: INVALID_ARG, CUDA. */
+lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, int nz, const double body_force[3],
+                           const alm_turbine_desc* desc, long long step, float* elem_force, float* elem_pos,
+                           double* loads, void* cuda_stream);
+
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);
 
