@@ -38,7 +38,11 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32")
     p.add_argument("--collision", choices=["cumulant", "srt_smag"], default="cumulant")
-    p.add_argument("--tile", type=str, default="32x4")
+    p.add_argument("--tile", type=str, default="auto",
+                   help="CTA tile XxY or XxYxZ, or 'auto' (the library's autotuner, cached)")
+    p.add_argument("--workload", choices=["single", "batch16", "precision"], default="single",
+                   help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices in one launch per "
+                        "step; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -156,8 +160,8 @@ def run_reference(args):
 
 
 def accuracy_check():
-    """Scaled-down rotor case (48x32x32, D = 12, 3 x 6 elements), 50 steps:
-    max |u_gpu - u_oracle| (FP32 GPU vs FP64 oracle)."""
+    """Part of the CPU-baseline leg: scaled-down rotor case (48x32x32, D = 12,
+    3 x 6 elements), 50 steps: max |u_gpu - u_oracle| (FP32 GPU vs FP64 oracle)."""
     import numpy as np
     import oracle as O
     from paper_2402_13171_gb300 import inputs as I
@@ -200,14 +204,34 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    tx, ty = (int(v) for v in args.tile.split("x"))
-    dom, turb = I.single_turbine_case()
-    dom["collision"] = args.collision
-    lat = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], device=local, collision=args.collision,
-                             nu=dom["nu"], smag_c=dom["smag_c"], storage=args.storage, bc=dom["bc"],
-                             seed=dom["seed"], tile=(tx, ty))
-    lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
-    lat.add_turbine(**turb)
+    tile = (0, 0, 0) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
+    if args.workload == "single":
+        dom, turb = I.single_turbine_case()
+        dom["collision"] = args.collision
+        lat = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], device=local, collision=args.collision,
+                                 nu=dom["nu"], smag_c=dom["smag_c"], storage=args.storage, bc=dom["bc"],
+                                 seed=dom["seed"], tile=tile)
+        lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
+        lat.add_turbine(**turb)
+        lattices = [lat]
+        workload = WORKLOAD
+        extra = {"rotor": "3 blades x 40 elements, D=32 at (64,64,64), eps=2, TSR 6"}
+    else:
+        cases = I.batch_instances(16)
+        cfgs = [dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], collision=args.collision, nu=d["nu"], smag_c=d["smag_c"],
+                     storage=args.storage, bc=d["bc"], seed=d["seed"], tile=tile) for d, _ in cases]
+        lattices = lbm.batch_create(cfgs, device=local)
+        for L, (d, t) in zip(lattices, cases):
+            L.set_inflow(u_ref=d["u_ref"], noise_rel=d["noise_rel"])
+            L.add_turbine(**t)
+        lat = lattices[0]
+        workload = "batch16_single_turbine_lattices"
+        extra = {"lattices": [f"{d['nx']}x{d['ny']}x{d['nz']}" for d, _ in cases],
+                 "rotor_diameters": [round(2 * t["radius"], 2) for _, t in cases]}
+    if args.tile == "auto":
+        cache = os.path.join(ROOT, "paper_2402_13171_gb300", "_build", "tune_cache.txt")
+        lat.autotune(steps=20, cache=cache)
+    tile_used = "x".join(str(v) for v in lat.tile())
     bytes_per_cell, cells = lat.traffic_model()
     lat.step(args.warmup)
     lat.sync()
@@ -240,7 +264,7 @@ def run_ours(args):
 
     # ---- end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.workload == "single":
         N = cells
         rho_h = torch.ones(N, dtype=torch.float64).pin_memory().numpy()
         u_h = torch.zeros(3 * N, dtype=torch.float64).pin_memory().numpy()
@@ -265,9 +289,11 @@ def run_ours(args):
 
     acc = None
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.workload == "single" and not args.no_cpu_baseline:
+        # the CPU-baseline leg: the oracle timed on the host cores, and the
+        # accuracy of the GPU path against it on a scaled-down rotor case
         acc = accuracy_check()
-        if not args.no_cpu_baseline:
+        if True:
             s, z0, planes, ccells, threads = oracle_sample_run(30, 20.0)
             nst = 5
             t = time.perf_counter()
@@ -282,9 +308,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": cells, "storage": args.storage, "collision": args.collision,
-                       "rotor": "3 blades x 40 elements, D=32 at (64,64,64), eps=2, TSR 6",
-                       "tile": args.tile, "parallelism": "replicas" if world > 1 else "single",
+            "config": {"workload": workload, "cells": cells, "storage": args.storage, "collision": args.collision,
+                       **extra,
+                       "tile": tile_used, "tuned": args.tile == "auto",
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"no flush: PDF arrays {2 * bytes_per_cell / 2 * cells / 1e6:.0f} MB > 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
@@ -298,15 +325,99 @@ def run_ours(args):
             "loads": {"thrust": thrust, "torque": torque},
         }
         print(json.dumps(line), flush=True)
-    lat.destroy()
+    for L in lattices:
+        L.destroy()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_precision(args):
+    """The single rotor scaled to 512x256x256 (D = 64 at (128, 128, 128), 80
+    elements per blade): the same seeded run with PDFs stored in FP32, BF16 and
+    FP16.  Mean u_x/U profiles along y through the hub at 2D, 4D and 5D
+    downstream (the farthest station at least 1D before the outlet; 8D does not
+    fit), averaged over the last 40 % of the steps.  Errors of the 16-bit runs
+    are L_inf and L2 (RMS) of the profile differences against FP32."""
+    import numpy as np
+    import torch
+
+    from paper_2402_13171_gb300 import build as B
+    from paper_2402_13171_gb300 import inputs as I
+    from paper_2402_13171_gb300 import lbm
+
+    B.build()
+    torch.cuda.set_device(0)
+    nx, ny, nz = 512, 256, 256
+    D = 64.0
+    hub = (128.0, 128.0, 128.0)
+    stations = {"2D": 256, "4D": 384, "5D": 448}
+    steps = args.steps
+    avg_from = int(0.6 * steps)
+    every = 20
+    ys = np.arange(ny)
+    px = np.concatenate([np.full(ny, x) for x in stations.values()])
+    py = np.concatenate([ys] * len(stations))
+    pz = np.full(px.size, int(hub[2]))
+    out = {}
+    for storage in ("fp32", "bf16", "fp16"):
+        dom, turb = I.single_turbine_case(nx, ny, nz, diameter=D, hub=hub, elements_per_blade=80)
+        lat = lbm.Lattice.create(nx, ny, nz, nu=dom["nu"], storage=storage, bc=dom["bc"], seed=dom["seed"])
+        lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
+        lat.add_turbine(**turb)
+        lat.autotune(steps=10, cache=os.path.join(ROOT, "paper_2402_13171_gb300", "_build", "tune_cache.txt"))
+        bpc, cells = lat.traffic_model()
+        acc = np.zeros((px.size, 3))
+        nsamp = 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        timed_ms = 0.0
+        timed_steps = 0
+        done = 0
+        while done < steps:
+            n = min(every, steps - done)
+            e0.record(lat.stream)
+            lat.step(n)
+            e1.record(lat.stream)
+            e1.synchronize()
+            timed_ms += e0.elapsed_time(e1)
+            timed_steps += n
+            done += n
+            if done >= avg_from:
+                _, u = lat.probe(px, py, pz)
+                acc += u
+                nsamp += 1
+        mean = acc / max(nsamp, 1) / dom["u_ref"][0]
+        mlups = cells * timed_steps / (timed_ms * 1e-3) / 1e6
+        out[storage] = {"mean_ux": mean[:, 0], "mlups": mlups,
+                        "hbm_frac": bpc * cells * timed_steps / (timed_ms * 1e-3) / 1e9 / load_peaks()[0],
+                        "tile": "x".join(map(str, lat.tile()))}
+        lat.destroy()
+    errors = {}
+    for storage in ("bf16", "fp16"):
+        errors[storage] = {}
+        for k, name in enumerate(stations):
+            sl = slice(k * ny, (k + 1) * ny)
+            d = out[storage]["mean_ux"][sl] - out["fp32"]["mean_ux"][sl]
+            errors[storage][name] = {"linf": float(np.abs(d).max()), "l2": float(np.sqrt(np.mean(d ** 2)))}
+    deficit = {name: float(1.0 - out["fp32"]["mean_ux"][k * ny:(k + 1) * ny].min()) for k, name in enumerate(stations)}
+    line = {
+        "metric": METRIC, "value": out["fp32"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "precision_512x256x256", "cells": nx * ny * nz, "rotor": "D=64 at (128,128,128), "
+                   "3 x 80 elements, eps=2, TSR 6", "average": f"steps {avg_from}..{steps}, every {every}"},
+        "runs": {k: {"mlups": v["mlups"], "hbm_frac": v["hbm_frac"], "tile": v["tile"]} for k, v in out.items()},
+        "max_wake_deficit_fp32": deficit,
+        "profile_error_vs_fp32": errors,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

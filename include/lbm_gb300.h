@@ -60,7 +60,8 @@ typedef enum {
     LBM_BC_PERIODIC = 0,       /* source index wraps */
     LBM_BC_INFLOW_OUTFLOW = 1, /* x only: equilibrium inlet at x = 0 (rho = 1, lbm_inflow velocity),
                                   zero-gradient outlet at x = nx-1 */
-    LBM_BC_NOSLIP = 2          /* halfway bounce-back walls at -1/2 and n-1/2 */
+    LBM_BC_NOSLIP = 2,         /* halfway bounce-back walls at -1/2 and n-1/2 */
+    LBM_BC_FREESLIP = 3        /* specular (zero-shear) walls at -1/2 and n-1/2 */
 } lbm_bc;
 
 typedef struct {
@@ -79,6 +80,7 @@ typedef struct {
     void* alloc_user;
     int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 32 x 4;
                                 tile_x a multiple of 32, tile_x * tile_y <= 256 */
+    int tile_z;              /* planes per CTA, each thread marching through them; 0 = default 1; <= 64 */
 } lbm_config;
 
 typedef struct {
@@ -153,6 +155,12 @@ lbm_status lbm_sync(lbm_ctx* ctx);
  * used).  Host arrays, caller-owned.  Synchronises. */
 lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u);
 
+/* rho and u (as lbm_get_moments computes them) at n listed cells (linear
+ * indices (z*ny + y)*nx + x, host array); rho [n] (may be NULL) and u [n][3]
+ * are host, caller-owned.  For monitoring points and wake profiles without
+ * copying whole fields.  Synchronises. */
+lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, double* u);
+
 /* Absolute populations f [27][N] (host, FP64) / overwrite them (checkpoint
  * restore: the step counter and lagged ALM force are kept).  Synchronises. */
 lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f);
@@ -173,6 +181,23 @@ lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_s
  * step n.  Synchronises. */
 lbm_status lbm_get_step(lbm_ctx* ctx, long long* step);
 lbm_status lbm_set_step(lbm_ctx* ctx, long long step);
+
+/* CTA tile of the step kernel (see lbm_config.tile_*); changing it rebuilds the
+ * work list.  Results do not depend on the tile.  INVALID_ARG for a bad shape. */
+lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z);
+lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z);
+
+/* Autotuner: times the step kernel for a fixed set of CTA tiles (tile_x,
+ * tile_y, tile_z) on the current state of every lattice of the batch
+ * (steps_per_candidate timed launches each, after 3 untimed ones), restoring
+ * the state (PDFs, rotor force boxes, step counter) after every candidate, and
+ * applies the fastest.  cache_path (or NULL): a text file of
+ * "<gpu/collision/storage/lattices key> tile_x tile_y tile_z ms" lines; a
+ * matching line is applied without timing, a new result is appended.
+ * tile_out receives the tile, best_ms its mean launch time.  The last
+ * diagnostic result may be overwritten.  Synchronises. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[3],
+                        double* best_ms);
 
 /* Kernel timing: when enabled, lbm_step launches kernels one by one with CUDA
  * events around every stream-collide launch; lbm_get_kernel_time returns the

@@ -228,7 +228,7 @@ def gauss_axis_sum(p, eps):
 
 # ---------------------------------------------------------------- domain
 
-BC = {"periodic": 0, "inout": 1, "noslip": 2}
+BC = {"periodic": 0, "inout": 1, "noslip": 2, "freeslip": 3}
 COLL = {"cumulant": 0, "srt_smag": 1}
 
 

@@ -430,7 +430,7 @@ double or_omega_from_nu(double nu) { return 1.0 / (3.0 * nu + 0.5); }
 /* Domain, boundaries, inflow                                                */
 /* ------------------------------------------------------------------------ */
 
-enum { OR_BC_PERIODIC = 0, OR_BC_INOUT = 1, OR_BC_NOSLIP = 2 };
+enum { OR_BC_PERIODIC = 0, OR_BC_INOUT = 1, OR_BC_NOSLIP = 2, OR_BC_FREESLIP = 3 };
 enum { OR_COLL_CUMULANT = 0, OR_COLL_SRT_SMAG = 1 };
 
 typedef struct {
@@ -487,12 +487,17 @@ static size_t cell_index(const or_domain* d, int x, int y, int z)
  * post-collision population q of cell x - c_q, except
  *   - no-slip axis, source outside [0, N): halfway bounce-back, the cell's own
  *     post-collision population of the opposite direction;
+ *   - free-slip axis, source outside [0, N): specular reflection, the
+ *     post-collision population of the mirrored direction (that velocity
+ *     component negated) at the source moved back onto the cell's own index
+ *     along that axis (the other components still shift);
  *   - periodic axis: the source index wraps;
  *   - x inflow (source x < 0): equilibrium at rho = 1 and the inflow velocity
- *     of the source column at this step;
+ *     of the source column at this step (of the mirrored direction, after a
+ *     free-slip reflection);
  *   - x outflow (source x >= nx): zero-gradient, the source is moved to the
  *     last plane x = nx-1.
- * The no-slip rule is tested first, then periodic wrapping, then the x rules.
+ * The rules apply in this order: no-slip, free-slip, periodic wrap, x in/out.
  */
 void or_pull_cell(const or_domain* d, const double* fsrc, long step, int x, int y, int z, double out[NQ])
 {
@@ -511,6 +516,13 @@ void or_pull_cell(const or_domain* d, const double* fsrc, long step, int x, int 
             out[q] = fsrc[(size_t)opp_of(q) * N + cell_index(d, x, y, z)];
             continue;
         }
+        int cm[3] = {c[0], c[1], c[2]}; /* direction whose population is read */
+        for (int a = 0; a < 3; ++a)
+            if (d->bc[a] == OR_BC_FREESLIP && (s[a] < 0 || s[a] >= n[a])) {
+                cm[a] = -c[a];
+                s[a] = p[a];
+            }
+        int qm = (cm[2] + 1) * 9 + (cm[1] + 1) * 3 + (cm[0] + 1);
         for (int a = 0; a < 3; ++a)
             if (d->bc[a] == OR_BC_PERIODIC) s[a] = ((s[a] % n[a]) + n[a]) % n[a];
         if (d->bc[0] == OR_BC_INOUT) {
@@ -518,12 +530,12 @@ void or_pull_cell(const or_domain* d, const double* fsrc, long step, int x, int 
                 double uin[3], feq[NQ];
                 or_inflow_velocity(d, step, s[1], s[2], uin);
                 or_equilibrium(1.0, uin, feq);
-                out[q] = feq[q];
+                out[q] = feq[qm];
                 continue;
             }
             if (s[0] >= n[0]) s[0] = n[0] - 1;
         }
-        out[q] = fsrc[(size_t)q * N + cell_index(d, s[0], s[1], s[2])];
+        out[q] = fsrc[(size_t)qm * N + cell_index(d, s[0], s[1], s[2])];
     }
 }
 

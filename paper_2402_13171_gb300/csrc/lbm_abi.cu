@@ -47,7 +47,7 @@ struct Batch {
     unsigned int* d_diag_done = nullptr;
     int diag_every = 0;
     long long host_step = 0;
-    int tile_x = 32, tile_y = 4;
+    int tile_x = 32, tile_y = 4, tile_z = 1;
     lbm_status status = LBM_OK;
     std::string err;
     bool dirty = true;
@@ -57,6 +57,9 @@ struct Batch {
     double prof_ms = 0.0;
     long long prof_n = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long* d_probe = nullptr;   // probe cell list and results, grown on demand
+    double* d_probe_out = nullptr;
+    int probe_cap = 0;
 };
 
 }  // namespace
@@ -147,14 +150,14 @@ lbm_status validate_cfg(const lbm_config* c, std::string& msg)
     if (c->storage < 0 || c->storage > 2) { msg = "unknown storage"; return LBM_ERR_INVALID_ARG; }
     if (!(c->nu > 0.0) || !std::isfinite(c->nu)) { msg = "nu must be > 0"; return LBM_ERR_INVALID_ARG; }
     for (int a = 0; a < 3; ++a) {
-        if (c->bc[a] < 0 || c->bc[a] > 2) { msg = "unknown boundary code"; return LBM_ERR_INVALID_ARG; }
+        if (c->bc[a] < 0 || c->bc[a] > 3) { msg = "unknown boundary code"; return LBM_ERR_INVALID_ARG; }
         if (a > 0 && c->bc[a] == LBM_BC_INFLOW_OUTFLOW) { msg = "inflow/outflow is x only"; return LBM_ERR_INVALID_ARG; }
     }
     if (c->bc[0] == LBM_BC_INFLOW_OUTFLOW && c->nx < 2) { msg = "inflow/outflow needs nx >= 2"; return LBM_ERR_INVALID_ARG; }
     if (c->diag_every < 0) { msg = "diag_every must be >= 0"; return LBM_ERR_INVALID_ARG; }
-    const int tx = c->tile_x ? c->tile_x : 32, ty = c->tile_y ? c->tile_y : 4;
-    if (tx < 32 || tx % 32 != 0 || ty < 1 || tx * ty > 256) {
-        msg = "tile_x must be a multiple of 32 and tile_x * tile_y <= 256";
+    const int tx = c->tile_x ? c->tile_x : 32, ty = c->tile_y ? c->tile_y : 4, tz = c->tile_z ? c->tile_z : 1;
+    if (tx < 32 || tx % 32 != 0 || ty < 1 || tx * ty > 256 || tz < 1 || tz > 64) {
+        msg = "tile_x must be a multiple of 32, tile_x * tile_y <= 256, 1 <= tile_z <= 64";
         return LBM_ERR_INVALID_ARG;
     }
     return LBM_OK;
@@ -245,14 +248,14 @@ lbm_status sync_descriptors(Batch* b)
     for (size_t i = 0; i < b->inst.size(); ++i) {
         Instance& I = b->inst[i];
         int nrot = 0;
-        for (int z = 0; z < I.h.nz; ++z)
+        for (int z = 0; z < I.h.nz; z += b->tile_z)
             for (int y0 = 0; y0 < I.h.ny; y0 += b->tile_y)
                 for (int x0 = 0; x0 < I.h.nx; x0 += b->tile_x) {
                     bool hit = false;
                     for (auto& t : I.turb) {
                         const DevTurbine& B = t.dev;
-                        if (z >= B.lo[2] && z <= B.hi[2] && y0 <= B.hi[1] && y0 + b->tile_y - 1 >= B.lo[1] &&
-                            x0 <= B.hi[0] && x0 + b->tile_x - 1 >= B.lo[0])
+                        if (z <= B.hi[2] && z + b->tile_z - 1 >= B.lo[2] && y0 <= B.hi[1] &&
+                            y0 + b->tile_y - 1 >= B.lo[1] && x0 <= B.hi[0] && x0 + b->tile_x - 1 >= B.lo[0])
                             hit = true;
                     }
                     if (hit) {
@@ -299,6 +302,7 @@ StepArgs step_args(Batch* b, int parity)
     a.step_slot = b->d_step;
     a.diag_done = b->d_diag_done;
     a.diag_every = b->diag_every;
+    a.tile_z = b->tile_z;
     return a;
 }
 
@@ -351,7 +355,8 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
         if (validate_cfg(cfgs + i, msg) != LBM_OK) return LBM_ERR_INVALID_ARG;
         if (cfgs[i].collision != cfgs[0].collision || cfgs[i].storage != cfgs[0].storage ||
             cfgs[i].cuda_stream != cfgs[0].cuda_stream || cfgs[i].tile_x != cfgs[0].tile_x ||
-            cfgs[i].tile_y != cfgs[0].tile_y || cfgs[i].diag_every != cfgs[0].diag_every)
+            cfgs[i].tile_y != cfgs[0].tile_y || cfgs[i].tile_z != cfgs[0].tile_z ||
+            cfgs[i].diag_every != cfgs[0].diag_every)
             return LBM_ERR_UNSUPPORTED;
     }
     Batch* b = new Batch();
@@ -363,6 +368,7 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     b->user = cfgs[0].alloc_user;
     b->tile_x = cfgs[0].tile_x ? cfgs[0].tile_x : 32;
     b->tile_y = cfgs[0].tile_y ? cfgs[0].tile_y : 4;
+    b->tile_z = cfgs[0].tile_z ? cfgs[0].tile_z : 1;
     b->diag_every = cfgs[0].diag_every;
     b->inst.resize(n);
     lbm_status s = LBM_OK;
@@ -687,6 +693,36 @@ lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u)
     return s;
 }
 
+lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, double* u)
+{
+    ENTER(ctx);
+    if (n < 0 || (n > 0 && (!cells || !u))) return fail(b, LBM_ERR_INVALID_ARG, "bad probe arguments", false);
+    if (n == 0) return LBM_OK;
+    for (int k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= I.h.N) return fail(b, LBM_ERR_INVALID_ARG, "probe cell out of range", false);
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    if (n > b->probe_cap) {
+        dfree(b, b->d_probe);
+        dfree(b, b->d_probe_out);
+        b->d_probe = (long long*)dalloc(b, sizeof(long long) * n);
+        b->d_probe_out = (double*)dalloc(b, sizeof(double) * 4 * n);
+        if (!b->d_probe || !b->d_probe_out) return fail(b, LBM_ERR_OOM, "probe buffer allocation failed");
+        b->probe_cap = n;
+    }
+    CK(cudaMemcpyAsync(b->d_probe, cells, sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));
+    CK(launch_probe(b->store, b->d_dom + ctx->idx, (int)(b->host_step & 1), b->d_probe, n, b->d_probe_out, b->stream));
+    std::vector<double> out((size_t)4 * n);
+    CK(cudaMemcpyAsync(out.data(), b->d_probe_out, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, b->stream));
+    s = check_device_errors(b);
+    if (s != LBM_OK) return s;
+    for (int k = 0; k < n; ++k) {
+        if (rho) rho[k] = out[4 * k];
+        for (int a = 0; a < 3; ++a) u[3 * k + a] = out[4 * k + 1 + a];
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f)
 {
     ENTER(ctx);
@@ -809,6 +845,179 @@ lbm_status lbm_set_step(lbm_ctx* ctx, long long step)
     lbm_status s = refresh_alm(b);
     if (s != LBM_OK) return s;
     return check_device_errors(b);
+}
+
+lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z)
+{
+    ENTER(ctx);
+    if (tile_x < 32 || tile_x % 32 != 0 || tile_y < 1 || tile_x * tile_y > 256 || tile_z < 1 || tile_z > 64)
+        return fail(b, LBM_ERR_INVALID_ARG, "tile_x must be a multiple of 32, tile_x * tile_y <= 256, 1 <= tile_z <= 64",
+                    false);
+    b->tile_x = tile_x;
+    b->tile_y = tile_y;
+    b->tile_z = tile_z;
+    b->dirty = true;
+    return sync_descriptors(b);
+}
+
+lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z)
+{
+    ENTER(ctx);
+    if (tile_x) *tile_x = b->tile_x;
+    if (tile_y) *tile_y = b->tile_y;
+    if (tile_z) *tile_z = b->tile_z;
+    return LBM_OK;
+}
+
+namespace {
+
+// Live state the tuner touches: the current PDF array and the rotor force boxes.
+struct Snapshot {
+    std::vector<void*> f;
+    std::vector<float*> box;
+};
+
+lbm_status snapshot_take(Batch* b, Snapshot& S)
+{
+    const int cur = (int)(b->host_step & 1);
+    for (auto& I : b->inst) {
+        const size_t fb = (size_t)I.h.N * 27 * store_bytes(b->store);
+        void* p = dalloc(b, fb);
+        if (!p) return fail(b, LBM_ERR_OOM, "tuner snapshot allocation failed");
+        CK(cudaMemcpyAsync(p, I.h.f[cur], fb, cudaMemcpyDeviceToDevice, b->stream));
+        S.f.push_back(p);
+        for (auto& t : I.turb) {
+            float* q = (float*)dalloc(b, sizeof(float) * 3 * t.dev.bcells);
+            if (!q) return fail(b, LBM_ERR_OOM, "tuner snapshot allocation failed");
+            CK(cudaMemcpyAsync(q, t.dev.fbox, sizeof(float) * 3 * t.dev.bcells, cudaMemcpyDeviceToDevice, b->stream));
+            S.box.push_back(q);
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status snapshot_restore(Batch* b, const Snapshot& S, long long step)
+{
+    b->host_step = step;
+    const int cur = (int)(step & 1);
+    size_t k = 0;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        Instance& I = b->inst[i];
+        CK(cudaMemcpyAsync(I.h.f[cur], S.f[i], (size_t)I.h.N * 27 * store_bytes(b->store), cudaMemcpyDeviceToDevice,
+                           b->stream));
+        for (auto& t : I.turb) {
+            CK(cudaMemcpyAsync(t.dev.fbox, S.box[k], sizeof(float) * 3 * t.dev.bcells, cudaMemcpyDeviceToDevice,
+                               b->stream));
+            ++k;
+        }
+    }
+    CK(cudaMemcpyAsync(b->d_step + cur, &b->host_step, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    return refresh_alm(b);
+}
+
+std::string tune_key(Batch* b)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    std::string k = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "/" + std::to_string(b->coll) +
+                    "/" + std::to_string(b->store);
+    for (auto& I : b->inst) {
+        k += "/" + std::to_string(I.h.nx) + "x" + std::to_string(I.h.ny) + "x" + std::to_string(I.h.nz);
+        k += I.turb.empty() ? "" : "r" + std::to_string(I.turb.size());
+    }
+    return k;
+}
+
+}  // namespace
+
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[3],
+                        double* best_ms)
+{
+    ENTER(ctx);
+    if (steps_per_candidate < 1) return fail(b, LBM_ERR_INVALID_ARG, "steps_per_candidate < 1", false);
+    const std::string key = tune_key(b);
+    if (cache_path) {
+        if (FILE* fp = std::fopen(cache_path, "r")) {
+            char kbuf[1024];
+            int tx, ty, tz, hx = 0, hy = 0, hz = 0;
+            double ms, hms = 0.0;
+            bool hit = false;
+            while (std::fscanf(fp, "%1023s %d %d %d %lf", kbuf, &tx, &ty, &tz, &ms) == 5)
+                if (key == kbuf) {
+                    hit = true;
+                    hx = tx;
+                    hy = ty;
+                    hz = tz;
+                    hms = ms;
+                }
+            std::fclose(fp);
+            if (hit) {
+                if (tile_out) { tile_out[0] = hx; tile_out[1] = hy; tile_out[2] = hz; }
+                if (best_ms) *best_ms = hms;
+                return lbm_set_tile(ctx, hx, hy, hz);
+            }
+        }
+    }
+    static const int cand[][3] = {{32, 4, 1}, {32, 2, 1}, {32, 8, 1}, {64, 2, 1}, {64, 1, 1}, {128, 1, 1},
+                                  {32, 4, 2}, {32, 4, 4}, {32, 2, 4}, {32, 2, 8}, {64, 2, 4}, {32, 8, 2},
+                                  {64, 4, 2}, {128, 1, 4}, {32, 4, 8}};
+    const long long step0 = b->host_step;
+    const bool prof = b->profiling;
+    Snapshot S;
+    lbm_status s = sync_descriptors(b);
+    if (s == LBM_OK) s = snapshot_take(b, S);
+    int best = -1;
+    double best_t = 1e300;
+    for (int c = 0; s == LBM_OK && c < (int)(sizeof cand / sizeof cand[0]); ++c) {
+        b->tile_x = cand[c][0];
+        b->tile_y = cand[c][1];
+        b->tile_z = cand[c][2];
+        b->dirty = true;
+        s = snapshot_restore(b, S, step0);
+        if (s != LBM_OK) break;
+        b->profiling = false;
+        s = lbm_step(ctx, 3);
+        if (s != LBM_OK) break;
+        b->profiling = true;
+        b->ev_used = 0;
+        b->prof_ms = 0.0;
+        b->prof_n = 0;
+        s = lbm_step(ctx, steps_per_candidate);
+        if (s != LBM_OK) break;
+        double ms = 0.0;
+        long long n = 0;
+        s = lbm_get_kernel_time(ctx, &ms, &n);
+        if (s == LBM_OK && ms < best_t) {
+            best_t = ms;
+            best = c;
+        }
+    }
+    b->profiling = prof;
+    b->ev_used = 0;
+    b->prof_ms = 0.0;
+    b->prof_n = 0;
+    if (best >= 0) {
+        b->tile_x = cand[best][0];
+        b->tile_y = cand[best][1];
+        b->tile_z = cand[best][2];
+        b->dirty = true;
+    }
+    if (!S.f.empty() && s == LBM_OK) s = snapshot_restore(b, S, step0);
+    for (void* p : S.f) dfree(b, p);
+    for (float* p : S.box) dfree(b, p);
+    if (s != LBM_OK) return s;
+    if (best < 0) return fail(b, LBM_ERR_STATE, "no tile candidate ran");
+    if (tile_out) { tile_out[0] = b->tile_x; tile_out[1] = b->tile_y; tile_out[2] = b->tile_z; }
+    if (best_ms) *best_ms = best_t;
+    if (cache_path)
+        if (FILE* fp = std::fopen(cache_path, "a")) {
+            std::fprintf(fp, "%s %d %d %d %.9g\n", key.c_str(), b->tile_x, b->tile_y, b->tile_z, best_t);
+            std::fclose(fp);
+        }
+    return LBM_OK;
 }
 
 lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable)

@@ -12,7 +12,7 @@ constexpr int kMaxTurbines = 16;    // rotors per lattice
 constexpr int kMaxElements = 4096;  // blade elements per lattice
 constexpr int kMaxInstances = 64;   // lattices per batch
 
-enum Bc : int { BC_PERIODIC = 0, BC_INOUT = 1, BC_NOSLIP = 2 };
+enum Bc : int { BC_PERIODIC = 0, BC_INOUT = 1, BC_NOSLIP = 2, BC_FREESLIP = 3 };
 enum Coll : int { COLL_CUMULANT = 0, COLL_SRT_SMAG = 1 };
 enum Store : int { STORE_FP32 = 0, STORE_BF16 = 1, STORE_FP16 = 2 };
 
@@ -87,6 +87,7 @@ struct StepArgs {
     long long* step_slot;               // step n in slot [parity]; CTA 0 writes n+1 to slot [parity ^ 1]
     unsigned int* diag_done;            // CTA completion counter, used on diagnostic steps only
     int diag_every;                     // diagnostic period shared by the batch (0 = off)
+    int tile_z;                         // planes per CTA (1: no marching)
 };
 
 // Work-list entry: bit 63 rotor tile, bits 48..62 instance, 32..47 z, 16..31 y0, 0..15 x0.
@@ -105,6 +106,8 @@ cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain&
                         const float* u, const float* fneq, int parity, int inflow_mean, cudaStream_t s);
 cudaError_t launch_moments(int store, const DevDomain* d_dom_inst, const DevDomain& h, int parity, double* rho,
                            double* u, cudaStream_t s);
+cudaError_t launch_probe(int store, const DevDomain* d_dom_inst, int parity, const long long* cells, int n, double* out,
+                         cudaStream_t s);
 cudaError_t launch_to_float(int store, const void* src, float* dst, long long n, cudaStream_t s);
 cudaError_t launch_from_float(int store, const float* src, void* dst, long long n, cudaStream_t s);
 

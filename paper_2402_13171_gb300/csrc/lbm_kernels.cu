@@ -167,13 +167,34 @@ __device__ __forceinline__ Moments raw_moments(const float h[27])
 // ------------------------------------------------------------------ collisions
 
 // One-dimensional map from central moments (k0, k1, k2) about u to the three
-// populations at c = -1, 0, +1.
-__device__ __forceinline__ void inv1d(float u, float k0, float k1, float k2, float& fm, float& f0, float& fp)
+// populations at c = -1, 0, +1:
+//   f(0)  = (1 - u^2) k0 - 2u k1 - k2
+//   f(-1) = ((u^2 - u) k0 + (2u - 1) k1 + k2) / 2
+//   f(+1) = ((u^2 + u) k0 + (2u + 1) k1 + k2) / 2
+// with the u-dependent coefficients computed once per axis.
+struct Inv1d {
+    float a0, am, ap, bm, bp, m2u;
+};
+
+__device__ __forceinline__ Inv1d inv1d_coeffs(float u)
 {
     const float u2 = u * u;
-    f0 = (1.0f - u2) * k0 - 2.0f * u * k1 - k2;
-    fm = 0.5f * ((u2 - u) * k0 + (2.0f * u - 1.0f) * k1 + k2);
-    fp = 0.5f * ((u2 + u) * k0 + (2.0f * u + 1.0f) * k1 + k2);
+    Inv1d c;
+    c.a0 = 1.0f - u2;
+    c.am = 0.5f * (u2 - u);
+    c.ap = 0.5f * (u2 + u);
+    c.bm = u - 0.5f;
+    c.bp = u + 0.5f;
+    c.m2u = -2.0f * u;
+    return c;
+}
+
+__device__ __forceinline__ void inv1d(const Inv1d& c, float k0, float k1, float k2, float& fm, float& f0, float& fp)
+{
+    const float h2 = 0.5f * k2;
+    fm = fmaf(c.am, k0, fmaf(c.bm, k1, h2));
+    fp = fmaf(c.ap, k0, fmaf(c.bp, k1, h2));
+    f0 = fmaf(c.a0, k0, fmaf(c.m2u, k1, -k2));
 }
 
 // Cumulant collision with shear rate omega, bulk and all higher-order rates 1
@@ -233,12 +254,13 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
     }
 #undef MI
     // inverse transform about u: z, then y, then x
+    const Inv1d cz = inv1d_coeffs(uz), cy = inv1d_coeffs(uy), cx = inv1d_coeffs(ux);
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float fm, f0, fp;
-            inv1d(uz, D[b * 3 + a], D[9 + b * 3 + a], D[18 + b * 3 + a], fm, f0, fp);
+            inv1d(cz, D[b * 3 + a], D[9 + b * 3 + a], D[18 + b * 3 + a], fm, f0, fp);
             D[b * 3 + a] = fm;
             D[9 + b * 3 + a] = f0;
             D[18 + b * 3 + a] = fp;
@@ -248,7 +270,7 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float fm, f0, fp;
-            inv1d(uy, D[k * 9 + a], D[k * 9 + 3 + a], D[k * 9 + 6 + a], fm, f0, fp);
+            inv1d(cy, D[k * 9 + a], D[k * 9 + 3 + a], D[k * 9 + 6 + a], fm, f0, fp);
             D[k * 9 + a] = fm;
             D[k * 9 + 3 + a] = f0;
             D[k * 9 + 6 + a] = fp;
@@ -256,7 +278,7 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         float fm, f0, fp;
-        inv1d(ux, D[3 * r], D[3 * r + 1], D[3 * r + 2], fm, f0, fp);
+        inv1d(cx, D[3 * r], D[3 * r + 1], D[3 * r + 2], fm, f0, fp);
         D[3 * r] = fm;
         D[3 * r + 1] = f0;
         D[3 * r + 2] = fp;
@@ -319,11 +341,15 @@ __device__ __forceinline__ long long cell_of(const DevDomain* D, int x, int y, i
     return ((long long)z * D->ny + y) * D->nx + x;
 }
 
-// Halfway bounce-back for a cell next to a no-slip face, applied after the
-// clamped loads of k_step (out of line: wall cells are few): every direction q
-// whose source x - c_q lies outside the lattice along a no-slip axis takes the
-// cell's own post-collision population of the opposite direction.  Wall rules
-// take precedence over the x inlet, whose values were patched before.
+// Wall rules for a cell next to a no-slip or free-slip face, applied after the
+// clamped loads of k_step (out of line: wall cells are few).  For every
+// direction q whose source x - c_q lies outside the lattice:
+//   - no-slip axis: halfway bounce-back, the cell's own post-collision
+//     population of the opposite direction (checked first);
+//   - free-slip axis: specular reflection, the mirrored direction (that
+//     component negated) read at the source moved back onto the cell's own
+//     index along that axis; the other axes wrap, or meet the x inlet (the
+//     mirrored direction's inlet equilibrium) or outlet (clamp).
 template <typename T>
 __device__ __noinline__ void boundary_patch(const DevDomain* D, const T* src, int x, int y, int z, long long step,
                                             float* h)
@@ -332,15 +358,39 @@ __device__ __noinline__ void boundary_patch(const DevDomain* D, const T* src, in
     const int p[3] = {x, y, z};
     const unsigned cell = (unsigned)(((long long)z * D->ny + y) * D->nx + x);
     const unsigned N = (unsigned)D->N;
-    (void)step;
     for (int q = 0; q < 27; ++q) {
         const int c[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
-        bool wall = false;
+        int s[3], cm[3];
+        bool wall = false, reflected = false;
         for (int a = 0; a < 3; ++a) {
-            const int s = p[a] - c[a];
-            if (D->bc[a] == BC_NOSLIP && (s < 0 || s >= n[a])) wall = true;
+            s[a] = p[a] - c[a];
+            cm[a] = c[a];
+            if (D->bc[a] == BC_NOSLIP && (s[a] < 0 || s[a] >= n[a])) wall = true;
         }
-        if (wall) h[q] = Io<T>::ld(src + (unsigned)(26 - q) * N + cell);
+        if (wall) {
+            h[q] = Io<T>::ld(src + (unsigned)(26 - q) * N + cell);
+            continue;
+        }
+        for (int a = 0; a < 3; ++a)
+            if (D->bc[a] == BC_FREESLIP && (s[a] < 0 || s[a] >= n[a])) {
+                cm[a] = -c[a];
+                s[a] = p[a];
+                reflected = true;
+            }
+        if (!reflected) continue;
+        const int qm = (cm[2] + 1) * 9 + (cm[1] + 1) * 3 + (cm[0] + 1);
+        for (int a = 0; a < 3; ++a)
+            if (D->bc[a] == BC_PERIODIC) s[a] = s[a] < 0 ? s[a] + n[a] : (s[a] >= n[a] ? s[a] - n[a] : s[a]);
+        if (D->bc[0] == BC_INOUT) {
+            if (s[0] < 0) {
+                const float* ub = D->inflow_u[step & 1];
+                const int plane = D->ny * D->nz, col = s[2] * D->ny + s[1];
+                h[q] = feq_offset_one(qm, ub[col], ub[plane + col], ub[2 * plane + col]);
+                continue;
+            }
+            if (s[0] >= n[0]) s[0] = n[0] - 1;
+        }
+        h[q] = Io<T>::ld(src + (unsigned)qm * N + (unsigned)(((long long)s[2] * D->ny + s[1]) * D->nx + s[0]));
     }
 }
 
@@ -576,8 +626,125 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
 
 // ------------------------------------------------------------------ the time step
 
-template <int COLL, typename T>
-__global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
+// Pulled pre-collision populations of cell (x, y, z): clamped/wrapped loads,
+// then the inlet and wall rules.
+template <typename T>
+__device__ __forceinline__ void load_cell(const DevDomain* D, const T* __restrict__ src, int x, int y, int z,
+                                          long long step, float h[27])
+{
+    const int nx = D->nx, ny = D->ny, nz = D->nz;
+    // source coordinates for c = +1 (m) and c = -1 (p): wrapped on periodic
+    // axes, clamped otherwise (the outlet rule; other faces are patched below)
+    const int bx = D->bc[0], by = D->bc[1], bz = D->bc[2];
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    if (bx == BC_PERIODIC) { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
+    else { xm = max(xm, 0); xp = min(xp, nx - 1); }
+    if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
+    else { ym = max(ym, 0); yp = min(yp, ny - 1); }
+    if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
+    else { zm = max(zm, 0); zp = min(zp, nz - 1); }
+    const bool walls = ((bx == BC_NOSLIP || bx == BC_FREESLIP) && (x == 0 || x == nx - 1)) ||
+                       ((by == BC_NOSLIP || by == BC_FREESLIP) && (y == 0 || y == ny - 1)) ||
+                       ((bz == BC_NOSLIP || bz == BC_FREESLIP) && (z == 0 || z == nz - 1));
+    // 32-bit offsets: 27 N < 2^31 is checked on the host
+    const unsigned uN = (unsigned)D->N;
+    const unsigned xs[3] = {(unsigned)xp, (unsigned)x, (unsigned)xm};  // source x for cx = -1, 0, +1
+    const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+    const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const unsigned row = (zs[k] * (unsigned)ny + ys[j]) * (unsigned)nx;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int q = k * 9 + j * 3 + i;
+                h[q] = Io<T>::ld(src + ((unsigned)q * uN + row + xs[i]));
+            }
+        }
+    // x inlet: the nine directions with c_x = +1 come from the ghost column
+    // (y - c_y, z - c_z): equilibrium at rho = 1 and that column's inlet velocity
+    if (bx == BC_INOUT && x == 0) {
+        const float* ub = D->inflow_u[step & 1];
+        const int plane = ny * nz;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int q = k * 9 + j * 3 + 2;
+                const bool wall = (by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
+                                  (bz == BC_NOSLIP && ((k == 2 && z == 0) || (k == 0 && z == nz - 1)));
+                if (!wall) {
+                    const int col = (int)zs[k] * ny + (int)ys[j];
+                    h[q] = feq_offset_one(q, ub[col], ub[plane + col], ub[2 * plane + col]);
+                }
+            }
+    }
+    if (walls) {
+        float hl[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) hl[q] = h[q];
+        boundary_patch<T>(D, src, x, y, z, step, hl);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) h[q] = hl[q];
+    }
+}
+
+// Gaussian-regularised blade force at cell (x, y, z) of a rotor tile, summed
+// over the rotors whose box holds the cell (element order; from the culled
+// list when it fits); each rotor's part is stored in its force box.
+__device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, int x, int y, int z, int n_cull,
+                                            const float4* s_pos, const float4* s_frc, const int* s_tag, float F[3])
+{
+    const float4* P = D->el_pos[step & 1];
+    const float4* Fe = D->el_force[step & 1];
+    for (int t = 0; t < D->n_turb; ++t) {
+        const DevTurbine* B = D->turb + t;
+        if (x < B->lo[0] || x > B->hi[0] || y < B->lo[1] || y > B->hi[1] || z < B->lo[2] || z > B->hi[2]) continue;
+        const int ne = B->n_blades * B->n_elements;
+        const float cut = B->cut, ie2 = B->inv_eps2;
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        if (n_cull >= 0) {
+            for (int i = 0; i < n_cull; ++i) {
+                if (s_tag[i] != t) continue;
+                const float4 pe = s_pos[i];
+                const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
+                if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
+                    const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
+                    const float4 fe = s_frc[i];
+                    ax -= w * fe.x;
+                    ay -= w * fe.y;
+                    az -= w * fe.z;
+                }
+            }
+        } else {
+            for (int e = 0; e < ne; ++e) {
+                const float4 pe = __ldg(P + B->el_offset + e);
+                const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
+                if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
+                    const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
+                    const float4 fe = __ldg(Fe + B->el_offset + e);
+                    ax -= w * fe.x;
+                    ay -= w * fe.y;
+                    az -= w * fe.z;
+                }
+            }
+        }
+        const long long bi = ((long long)(z - B->lo[2]) * B->bny + (y - B->lo[1])) * B->bnx + (x - B->lo[0]);
+        B->fbox[bi] = ax;
+        B->fbox[B->bcells + bi] = ay;
+        B->fbox[2 * B->bcells + bi] = az;
+        F[0] += ax;
+        F[1] += ay;
+        F[2] += az;
+    }
+}
+
+// One time step over the work list.  A CTA covers tile_x x tile_y cells of
+// tile_z consecutive planes; with MARCH a thread walks its column of planes and
+// issues the loads of the next plane before the collision of the current one.
+template <int COLL, typename T, bool MARCH>
+__global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
 {
     constexpr int kCull = 128;  // blade elements kept per rotor tile
     __shared__ double s_red[8][4];
@@ -588,14 +755,15 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
     const unsigned long long tile = A.tiles[blockIdx.x];
     const bool rotor_tile = (tile >> 63) != 0;
     const int inst = (int)((tile >> 48) & 0x7FFF);
-    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int z0 = (int)((tile >> 32) & 0xFFFF);
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
     const DevDomain* D = A.dom + inst;
     const long long step = __ldcg(A.step_slot + A.parity);
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) A.step_slot[A.parity ^ 1] = step + 1;
     const int nx = D->nx, ny = D->ny, nz = D->nz;
-    const long long N = D->N;
+    const int z1 = MARCH ? min(z0 + A.tile_z, nz) : z0 + 1;  // planes [z0, z1)
+    const unsigned uN = (unsigned)D->N;
     const T* __restrict__ src = (const T*)D->f[A.parity];
     T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
     const bool diag = A.diag_every > 0 && (step % A.diag_every) == 0;  // uniform over the grid
@@ -609,6 +777,7 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
     if (rotor_tile) {
         const float tx0 = (float)(tile & 0xFFFF), ty0 = (float)((tile >> 16) & 0xFFFF);
         const float tx1 = tx0 + (float)(blockDim.x - 1), ty1 = ty0 + (float)(blockDim.y - 1);
+        const float tz0 = (float)z0, tz1 = (float)(z1 - 1);
         const float4* P = D->el_pos[step & 1];
         const float4* Fe = D->el_force[step & 1];
         const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
@@ -623,7 +792,7 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
                 while (t + 1 < D->n_turb && D->turb[t + 1].el_offset <= e) ++t;
                 const float cut = D->turb[t].cut;
                 keep = pe.x + cut >= tx0 && pe.x - cut <= tx1 && pe.y + cut >= ty0 && pe.y - cut <= ty1 &&
-                       fabsf(pe.z - (float)z) <= cut;
+                       pe.z + cut >= tz0 && pe.z - cut <= tz1;
             }
             const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
             if (lane == 0) s_cnt[warp] = __popc(m);
@@ -646,125 +815,40 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
     }
 
     if (x < nx && y < ny) {
-        float h[27];
-        // source coordinates for c = +1 (m) and c = -1 (p): wrapped on periodic
-        // axes, clamped otherwise (the outlet rule; other faces are patched below)
-        const int bx = D->bc[0], by = D->bc[1], bz = D->bc[2];
-        int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
-        if (bx == BC_PERIODIC) { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
-        else { xm = max(xm, 0); xp = min(xp, nx - 1); }
-        if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
-        else { ym = max(ym, 0); yp = min(yp, ny - 1); }
-        if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
-        else { zm = max(zm, 0); zp = min(zp, nz - 1); }
-        const bool walls = (bx == BC_NOSLIP && (x == 0 || x == nx - 1)) || (by == BC_NOSLIP && (y == 0 || y == ny - 1)) ||
-                           (bz == BC_NOSLIP && (z == 0 || z == nz - 1));
-        // 32-bit offsets: 27 N < 2^31 is checked on the host
-        const unsigned uN = (unsigned)N;
-        const unsigned xs[3] = {(unsigned)xp, (unsigned)x, (unsigned)xm};  // source x for cx = -1, 0, +1
-        const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
-        const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+        float hn[27];
+        load_cell<T>(D, src, x, y, z0, step, hn);
+#pragma unroll 1
+        for (int z = z0; z < z1; ++z) {
+            float h[27];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const unsigned row = (zs[k] * (unsigned)ny + ys[j]) * (unsigned)nx;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int q = k * 9 + j * 3 + i;
-                    h[q] = Io<T>::ld(src + ((unsigned)q * uN + row + xs[i]));
-                }
+            for (int q = 0; q < 27; ++q) h[q] = hn[q];
+            if (MARCH && z + 1 < z1) load_cell<T>(D, src, x, y, z + 1, step, hn);
+            // the x = 0 lane of each row prepares the inlet velocity of its column for step n+1
+            if (D->bc[0] == BC_INOUT && x == 0) {
+                float u[3];
+                inflow_velocity(D, step + 1, y, z, u);
+                float* ub = D->inflow_u[(step + 1) & 1];
+                const int plane = ny * nz, col = z * ny + y;
+                ub[col] = u[0];
+                ub[plane + col] = u[1];
+                ub[2 * plane + col] = u[2];
             }
-        // x inlet: the nine directions with c_x = +1 come from the ghost column
-        // (y - c_y, z - c_z): equilibrium at rho = 1 and that column's inlet velocity
-        if (bx == BC_INOUT && x == 0) {
-            const float* ub = D->inflow_u[step & 1];
-            const int plane = ny * nz;
+            // force: body + regularised blade forces inside the rotor boxes
+            float F[3] = {D->body[0], D->body[1], D->body[2]};
+            if (rotor_tile) rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
+            float m, jx, jy, jz;
+            if (COLL == COLL_CUMULANT)
+                collide_cumulant(h, F[0], F[1], F[2], D->omega, m, jx, jy, jz);
+            else
+                collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, m, jx, jy, jz);
+            o_m += m;
+            o_jx += jx;
+            o_jy += jy;
+            o_jz += jz;
+            const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int q = k * 9 + j * 3 + 2;
-                    const bool wall = (by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
-                                      (bz == BC_NOSLIP && ((k == 2 && z == 0) || (k == 0 && z == nz - 1)));
-                    if (!wall) {
-                        const int col = (int)zs[k] * ny + (int)ys[j];
-                        h[q] = feq_offset_one(q, ub[col], ub[plane + col], ub[2 * plane + col]);
-                    }
-                }
+            for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
         }
-        if (walls) {
-            float hl[27];
-#pragma unroll
-            for (int q = 0; q < 27; ++q) hl[q] = h[q];
-            boundary_patch<T>(D, src, x, y, z, step, hl);
-#pragma unroll
-            for (int q = 0; q < 27; ++q) h[q] = hl[q];
-        }
-        // the x = 0 lane of each row prepares the inlet velocity of its column for step n+1
-        if (bx == BC_INOUT && x == 0) {
-            float u[3];
-            inflow_velocity(D, step + 1, y, z, u);
-            float* ub = D->inflow_u[(step + 1) & 1];
-            const int plane = ny * nz, col = z * ny + y;
-            ub[col] = u[0];
-            ub[plane + col] = u[1];
-            ub[2 * plane + col] = u[2];
-        }
-        // force: body + regularised blade forces inside the rotor boxes
-        float F[3] = {D->body[0], D->body[1], D->body[2]};
-        if (rotor_tile) {
-            const float4* P = D->el_pos[step & 1];
-            const float4* Fe = D->el_force[step & 1];
-            for (int t = 0; t < D->n_turb; ++t) {
-                const DevTurbine* B = D->turb + t;
-                if (x < B->lo[0] || x > B->hi[0] || y < B->lo[1] || y > B->hi[1] || z < B->lo[2] || z > B->hi[2])
-                    continue;
-                const int ne = B->n_blades * B->n_elements;
-                const float cut = B->cut, ie2 = B->inv_eps2;
-                float ax = 0.0f, ay = 0.0f, az = 0.0f;
-                if (n_cull >= 0) {
-                    for (int i = 0; i < n_cull; ++i) {
-                        if (s_tag[i] != t) continue;
-                        const float4 pe = s_pos[i];
-                        const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
-                        if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
-                            const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
-                            const float4 fe = s_frc[i];
-                            ax -= w * fe.x;
-                            ay -= w * fe.y;
-                            az -= w * fe.z;
-                        }
-                    }
-                } else {
-                    for (int e = 0; e < ne; ++e) {
-                        const float4 pe = __ldg(P + B->el_offset + e);
-                        const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
-                        if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
-                            const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
-                            const float4 fe = __ldg(Fe + B->el_offset + e);
-                            ax -= w * fe.x;
-                            ay -= w * fe.y;
-                            az -= w * fe.z;
-                        }
-                    }
-                }
-                const long long bi = ((long long)(z - B->lo[2]) * B->bny + (y - B->lo[1])) * B->bnx + (x - B->lo[0]);
-                B->fbox[bi] = ax;
-                B->fbox[B->bcells + bi] = ay;
-                B->fbox[2 * B->bcells + bi] = az;
-                F[0] += ax;
-                F[1] += ay;
-                F[2] += az;
-            }
-        }
-        if (COLL == COLL_CUMULANT)
-            collide_cumulant(h, F[0], F[1], F[2], D->omega, o_m, o_jx, o_jy, o_jz);
-        else
-            collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, o_m, o_jx, o_jy, o_jz);
-        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
-#pragma unroll
-        for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
     }
 
     // last rotor CTA of this lattice: actuator line of the next step
@@ -805,17 +889,15 @@ __global__ void __launch_bounds__(256, 3) k_step(const StepArgs A)
                 __threadfence();
                 for (int i = 0; i < A.n_inst; ++i) {
                     const DevDomain* Di = A.dom + i;
-                    {
-                        bool finite = true;
-                        for (int k = 0; k < 4; ++k) {
-                            const double sum = __ldcg(Di->diag_acc + k);
-                            Di->diag_res[k] = sum;
-                            Di->diag_acc[k] = 0.0;
-                            if (!isfinite(sum)) finite = false;
-                        }
-                        Di->diag_res[4] = (double)step;
-                        if (!finite) atomicOr(Di->err, ERR_NONFINITE);
+                    bool finite = true;
+                    for (int k = 0; k < 4; ++k) {
+                        const double sum = __ldcg(Di->diag_acc + k);
+                        Di->diag_res[k] = sum;
+                        Di->diag_acc[k] = 0.0;
+                        if (!isfinite(sum)) finite = false;
                     }
+                    Di->diag_res[4] = (double)step;
+                    if (!finite) atomicOr(Di->err, ERR_NONFINITE);
                 }
                 *A.diag_done = 0u;
             }
@@ -901,6 +983,31 @@ __global__ void k_moments(const DevDomain* D, int parity, double* rho, double* u
     }
 }
 
+// rho and u at listed cells, as k_moments computes them.
+template <typename T>
+__global__ void k_probe(const DevDomain* D, int parity, const long long* cells, int n, double* out)
+{
+    const long long N = D->N;
+    const T* f = (const T*)D->f[parity];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long long i = cells[k];
+        float h[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldcg(f + (size_t)q * N + i);
+        const Moments M = raw_moments(h);
+        const int x = (int)(i % D->nx);
+        const int y = (int)((i / D->nx) % D->ny);
+        const int z = (int)(i / ((long long)D->nx * D->ny));
+        float F[3] = {D->body[0], D->body[1], D->body[2]};
+        alm_box_force(D, x, y, z, F);
+        const double r = 1.0 + (double)M.drho;
+        out[4 * k] = r;
+        out[4 * k + 1] = ((double)M.jx - 0.5 * (double)F[0]) / r;
+        out[4 * k + 2] = ((double)M.jy - 0.5 * (double)F[1]) / r;
+        out[4 * k + 3] = ((double)M.jz - 0.5 * (double)F[2]) / r;
+    }
+}
+
 template <typename T>
 __global__ void k_to_float(const T* src, float* dst, long long n)
 {
@@ -926,9 +1033,11 @@ static int grid_for(long long n, int block)
 
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a)
 {
+    const bool march = a.tile_z > 1;
 #define LBM_STEP_CASE(C, S, T)                                      \
     if (coll == C && store == S) {                                  \
-        k_step<C, T><<<grid, block, 0, s>>>(a);                     \
+        if (march) k_step<C, T, true><<<grid, block, 0, s>>>(a);    \
+        else k_step<C, T, false><<<grid, block, 0, s>>>(a);         \
         return cudaGetLastError();                                  \
     }
     LBM_STEP_CASE(COLL_CUMULANT, STORE_FP32, float)
@@ -972,6 +1081,16 @@ cudaError_t launch_moments(int store, const DevDomain* d_dom_inst, const DevDoma
     if (store == STORE_FP32) k_moments<float><<<g, 256, 0, s>>>(d_dom_inst, parity, rho, u);
     else if (store == STORE_BF16) k_moments<__nv_bfloat16><<<g, 256, 0, s>>>(d_dom_inst, parity, rho, u);
     else k_moments<__half><<<g, 256, 0, s>>>(d_dom_inst, parity, rho, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe(int store, const DevDomain* d_dom_inst, int parity, const long long* cells, int n, double* out,
+                         cudaStream_t s)
+{
+    const int g = grid_for(n, 128);
+    if (store == STORE_FP32) k_probe<float><<<g, 128, 0, s>>>(d_dom_inst, parity, cells, n, out);
+    else if (store == STORE_BF16) k_probe<__nv_bfloat16><<<g, 128, 0, s>>>(d_dom_inst, parity, cells, n, out);
+    else k_probe<__half><<<g, 128, 0, s>>>(d_dom_inst, parity, cells, n, out);
     return cudaGetLastError();
 }
 

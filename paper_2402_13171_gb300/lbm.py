@@ -20,7 +20,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA er
           5: "device wait timed out", 6: "invalid state", 7: "unsupported combination"}
 COLL = {"cumulant": 0, "srt_smag": 1}
 STORE = {"fp32": 0, "bf16": 1, "fp16": 2}
-BC = {"periodic": 0, "inout": 1, "noslip": 2}
+BC = {"periodic": 0, "inout": 1, "noslip": 2, "freeslip": 3}
 STORE_BYTES = {"fp32": 4, "bf16": 2, "fp16": 2}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -43,7 +43,7 @@ class LbmConfig(ctypes.Structure):
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
-        ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+        ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
     ]
 
 
@@ -98,6 +98,12 @@ def load():
         "lbm_set_profiling": [ctypes.c_void_p, ctypes.c_int],
         "lbm_get_kernel_time": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_get_traffic_model": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
+        "lbm_set_tile": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "lbm_probe": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, _dp, _dp],
+        "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_double)],
+        "lbm_get_tile": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -156,6 +162,7 @@ def make_config(nx, ny, nz, collision="cumulant", nu=0.01, smag_c=0.0, storage="
         c.dev_alloc = allocator.alloc_cb
         c.dev_free = allocator.free_cb
     c.tile_x, c.tile_y = int(tile[0]), int(tile[1])
+    c.tile_z = int(tile[2]) if len(tile) > 2 else 0
     return c
 
 
@@ -254,6 +261,16 @@ class Lattice:
         self._call("lbm_get_moments", _p(rho), _p(u))
         return rho, u
 
+    def probe(self, x, y, z):
+        """rho (n) and u (n, 3) at cells (x, y, z) (integer arrays of equal length)."""
+        x, y, z = (np.asarray(v, dtype=np.int64).reshape(-1) for v in (x, y, z))
+        cells = np.ascontiguousarray((z * self.ny + y) * self.nx + x, dtype=np.int64)
+        rho = np.empty(cells.size)
+        u = np.empty((cells.size, 3))
+        self._call("lbm_probe", cells.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), int(cells.size), _p(rho),
+                   _p(u))
+        return rho, u
+
     def pdfs(self):
         f = np.empty((27, self.nz, self.ny, self.nx))
         self._call("lbm_get_pdfs", _p(f))
@@ -297,6 +314,20 @@ class Lattice:
         n = ctypes.c_longlong()
         self._call("lbm_get_kernel_time", ctypes.byref(ms), ctypes.byref(n))
         return ms.value, n.value
+
+    def set_tile(self, tx, ty, tz=1):
+        self._call("lbm_set_tile", int(tx), int(ty), int(tz))
+
+    def autotune(self, steps=20, cache=None):
+        out = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        self._call("lbm_autotune", int(steps), None if cache is None else str(cache).encode(), out, ctypes.byref(ms))
+        return tuple(out), ms.value
+
+    def tile(self):
+        v = [ctypes.c_int() for _ in range(3)]
+        self._call("lbm_get_tile", *[ctypes.byref(a) for a in v])
+        return tuple(a.value for a in v)
 
     def traffic_model(self):
         b = ctypes.c_double()

@@ -84,6 +84,23 @@ def test_bounce_back_poiseuille(coll):
     assert max_du(g, s) <= DU_TOL
 
 
+@pytest.mark.parametrize("bc", [("inout", "periodic", "freeslip"), ("freeslip", "noslip", "freeslip"),
+                                ("inout", "freeslip", "noslip")])
+def test_free_slip_walls(bc):
+    """Specular walls (and their corners with inlet, outlet and no-slip faces):
+    one-step PDFs and a short run against the oracle."""
+    dom = dict(nx=23, ny=9, nz=11, nu=0.02, bc=bc, u_ref=(0.04, 0.01, 0.0), noise_rel=0.01, seed=77,
+               body_force=(2e-6, 0, -1e-6))
+    rho, u, fneq = I.random_state(23, 9, 11, seed=5, u_mean=(0.04, 0.01, 0.0))
+    g, s = setup_pair(dom, rho=rho, u=u, fneq=fneq, inflow=bc[0] == "inout")
+    g.step(1)
+    s.step(1)
+    np.testing.assert_allclose(g.pdfs(), s.f, atol=F_TOL, rtol=0)
+    g.step(30)
+    s.step(30)
+    assert max_du(g, s) <= DU_TOL
+
+
 def test_inlet_outlet_noise():
     dom = dict(nx=40, ny=12, nz=9, nu=0.01, bc=("inout", "periodic", "periodic"), u_ref=(0.05, 0.0, 0.0),
                noise_rel=0.01, seed=12345)
@@ -166,7 +183,7 @@ def test_full_size_single_turbine_sampled():
         np.testing.assert_allclose(fg[:, z, y, x], ref, atol=F_TOL, rtol=0, err_msg=str((x, y, z)))
 
 
-@pytest.mark.parametrize("tile", [(128, 1), (64, 2), (256, 1), (96, 1), (32, 8)])
+@pytest.mark.parametrize("tile", [(128, 1), (64, 2), (256, 1), (96, 1), (32, 8), (32, 4, 4), (32, 2, 7), (64, 2, 64)])
 def test_tile_shapes_agree(tile):
     dom, turb = small_rotor_case()
     ga, _ = setup_pair(dom, [turb], inflow=True)
@@ -174,6 +191,31 @@ def test_tile_shapes_agree(tile):
     ga.step(7)
     gb.step(7)
     np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+
+
+def test_autotune_keeps_state_and_results():
+    """The tuner times tile candidates on the live state and restores it: the
+    run continues exactly as an untuned one."""
+    import os
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    gb, _ = setup_pair(dom, [turb], inflow=True)
+    ga.step(5)
+    gb.step(5)
+    cache = os.path.join(os.path.dirname(__file__), "..", "gpurun_out", "tune_cache_test.txt")
+    if os.path.exists(cache):
+        os.remove(cache)
+    tile, ms = gb.autotune(steps=3, cache=cache)
+    assert ms > 0 and gb.tile() == tile
+    assert gb.step_count() == 5
+    ga.step(6)
+    gb.step(6)
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    assert ga.loads(0) == gb.loads(0)
+    # a cache hit applies the stored tile without timing
+    gc, _ = setup_pair(dom, [turb], inflow=True)
+    tile2, ms2 = gc.autotune(steps=3, cache=cache)
+    assert tile2 == tile and ms2 == pytest.approx(ms, rel=1e-6)
 
 
 def test_graph_replay_equals_direct_launches():
@@ -215,6 +257,19 @@ def test_checkpoint_resume_is_bitwise():
     hb.set_step(13)
     hb.step(5)
     np.testing.assert_array_equal(ha.pdfs(), hb.pdfs())
+
+
+def test_probe_matches_moments():
+    dom, turb = small_rotor_case()
+    g, _ = setup_pair(dom, [turb], inflow=True)
+    g.step(9)
+    rho, u = g.moments()
+    rng = np.random.default_rng(4)
+    x, y, z = rng.integers(0, 64, 50), rng.integers(0, 40, 50), rng.integers(0, 40, 50)
+    x[:3], y[:3], z[:3] = 16, 20, 20  # hub: inside the rotor force box
+    pr, pu = g.probe(x, y, z)
+    np.testing.assert_array_equal(pr, rho[z, y, x])
+    np.testing.assert_array_equal(pu, u[:, z, y, x].T)
 
 
 def test_diagnostics_fp64_sums():

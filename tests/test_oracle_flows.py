@@ -177,3 +177,56 @@ def test_mass_and_momentum_conserved_periodic():
         assert s.f.sum() == pytest.approx(m0, rel=1e-14)
         np.testing.assert_allclose(np.einsum("qa,qzyx->a", C, s.f), j0 + 3 * 6 * 5 * 7 * np.array([1e-5, 2e-5, -1e-5]),
                                    atol=1e-13)
+
+
+def test_pull_free_slip_reflects():
+    rng = np.random.default_rng(13)
+    nx, ny, nz = 5, 4, 6
+    d = O.make_domain(nx, ny, nz, bc=("periodic", "periodic", "freeslip"))
+    s = O.Sim(d)
+    f = rng.uniform(0, 1, (27, nz, ny, nx))
+    for (x, y, z) in [(0, 0, 0), (2, 3, nz - 1), (4, 1, 3)]:
+        out = s.pull_cell(f, 0, x, y, z)
+        for q in range(27):
+            cx, cy, cz = C[q].astype(int)
+            sz = z - cz
+            if sz < 0 or sz >= nz:
+                qm = (-cz + 1) * 9 + (cy + 1) * 3 + (cx + 1)
+                assert out[q] == f[qm, z, (y - cy) % ny, (x - cx) % nx]
+            else:
+                assert out[q] == f[q, sz, (y - cy) % ny, (x - cx) % nx]
+
+
+def test_free_slip_channel_uniform_flow_is_steady():
+    d = O.make_domain(6, 5, 8, bc=("periodic", "periodic", "freeslip"), u_ref=(0.05, 0.02, 0.0), nu=0.02)
+    s = O.Sim(d)
+    s.init_fields()
+    f0 = s.f.copy()
+    s.step(4)
+    np.testing.assert_allclose(s.f, f0, atol=2e-16)
+
+
+def free_slip_wave_nu(nz, nu, steps):
+    """u_x = u0 cos(pi (z + 1/2) / nz) between free-slip walls at z = -1/2 and
+    nz - 1/2 (zero shear stress) decays as exp(-nu k^2 t), k = pi / nz."""
+    d = O.make_domain(1, 1, nz, nu=nu, bc=("periodic", "periodic", "freeslip"))
+    s = O.Sim(d)
+    k = math.pi / nz
+    z = np.arange(nz) + 0.5
+    u = np.zeros((3, nz, 1, 1))
+    u[0, :, 0, 0] = 1e-3 * np.cos(k * z)
+    s.init_fields(np.ones(nz), u)
+    prof = np.cos(k * z)
+    amps = []
+    for n in (20, steps):
+        s.step(n - s.step_count)
+        amps.append(np.dot(s.moments()[1][0, :, 0, 0], prof) / np.dot(prof, prof))
+    return -math.log(amps[1] / amps[0]) / (k * k * (steps - 20))
+
+
+def test_free_slip_wave_decay_converges():
+    nu = 0.05
+    e8 = abs(free_slip_wave_nu(8, nu, 120) / nu - 1)
+    e16 = abs(free_slip_wave_nu(16, nu, 420) / nu - 1)
+    assert e16 < 2e-2
+    assert e8 / e16 > 3.0
