@@ -39,10 +39,12 @@ def parse_args():
     p.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32")
     p.add_argument("--collision", choices=["cumulant", "srt_smag"], default="cumulant")
     p.add_argument("--tile", type=str, default="auto",
-                   help="CTA tile XxY or XxYxZ, or 'auto' (the library's autotuner, cached)")
-    p.add_argument("--workload", choices=["single", "batch16", "precision"], default="single",
+                   help="CTA tile XxY, XxYxZ or XxYxZxS (S = 1: rows staged in shared memory), or 'auto' "
+                        "(the library's autotuner, cached)")
+    p.add_argument("--workload", choices=["single", "batch16", "precision", "warmstart"], default="single",
                    help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices in one launch per "
-                        "step; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles")
+                        "step; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles; "
+                        "warmstart: 3x3 farm, steps to a settled mean from a cold vs a surrogate warm start")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -204,7 +206,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    tile = (0, 0, 0) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
+    tile = (0, 0, 0, 0) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
     if args.workload == "single":
         dom, turb = I.single_turbine_case()
         dom["collision"] = args.collision
@@ -231,7 +233,8 @@ def run_ours(args):
     if args.tile == "auto":
         cache = os.path.join(ROOT, "paper_2402_13171_gb300", "_build", "tune_cache.txt")
         lat.autotune(steps=20, cache=cache)
-    tile_used = "x".join(str(v) for v in lat.tile())
+    tx_, ty_, tz_, st_ = lat.tile()
+    tile_used = f"{tx_}x{ty_}x{tz_}" + (" staged" if st_ else "")
     bytes_per_cell, cells = lat.traffic_model()
     lat.step(args.warmup)
     lat.sync()
@@ -390,7 +393,7 @@ def run_precision(args):
         mlups = cells * timed_steps / (timed_ms * 1e-3) / 1e6
         out[storage] = {"mean_ux": mean[:, 0], "mlups": mlups,
                         "hbm_frac": bpc * cells * timed_steps / (timed_ms * 1e-3) / 1e9 / load_peaks()[0],
-                        "tile": "x".join(map(str, lat.tile()))}
+                        "tile": "x".join(map(str, lat.tile()[:3])) + (" staged" if lat.tile()[3] else "")}
         lat.destroy()
     errors = {}
     for storage in ("bf16", "fp16"):
@@ -412,12 +415,95 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start on the 3x3 farm: 1024x384x192 cells, rotors D = 48
+    in rows x = 96, 336, 576 and columns y = 48, 192, 336 at hub height 96,
+    seeded yaw in [0, 10] degrees, TSR 6; log-law inflow
+    u(z) = 0.05 ln(z_c/0.1)/ln(96/0.1) with 1 % noise, free-slip top and
+    bottom, periodic y.  The surrogate (6 -> 4 x 128 GELU -> 3, BF16 weights)
+    is trained on the mean wakes of 64 single-rotor runs of this solver.  The
+    farm runs from the inflow profile (cold, --steps steps; its second half
+    gives the converged mean and its noise floor) and from the surrogate's
+    superposed wakes (warm, --steps/2); each settles at the first 1000-step
+    window of hub-plane u_x within twice the noise floor of the converged mean."""
+    import numpy as np
+    import torch
+
+    from paper_2402_13171_gb300 import build as B
+    from paper_2402_13171_gb300 import inputs as I
+    from paper_2402_13171_gb300 import lbm
+    from paper_2402_13171_gb300 import surrogate as S
+
+    B.build()
+    torch.cuda.set_device(0)
+    t = time.perf_counter()
+    X, T, runs = S.generate_wake_data(64, seed=31, shape=(192, 96, 96), D=24.0, spinup=2000, average=2000, every=20)
+    t_data = time.perf_counter() - t
+    net = S.WakeMLP(seed=4)
+    net.set_data(X, T)
+    t = time.perf_counter()
+    loss = net.train(3000, batch=4096, lr=1e-3, seed=9)
+    t_train = time.perf_counter() - t
+    nx, ny, nz, D = 1024, 384, 192, 48.0
+    rng = np.random.default_rng(2402131715)
+    zc = np.arange(nz) + 0.5
+    Uz = 0.05 * np.log(zc / 0.1) / np.log(96.0 / 0.1)
+    u_hub = float(0.05 * np.log(96.5 / 0.1) / np.log(96.0 / 0.1))
+    rotors = [dict(hub=(float(x), float(y), 96.0), D=D, tsr=6.0, yaw=float(np.radians(rng.uniform(0, 10))),
+                   u_hub=u_hub) for x in (96, 336, 576) for y in (48, 192, 336)]
+    cache = os.path.join(ROOT, "paper_2402_13171_gb300", "_build", "tune_cache.txt")
+    result = {}
+    wms = {}
+    for mode in ("cold", "warm"):
+        lat = lbm.Lattice.create(nx, ny, nz, nu=1e-3, bc=("inout", "periodic", "freeslip"), seed=2402131715)
+        lat.set_inflow(u_ref=(0.05, 0.0, 0.0), kind=1, z0=0.1, z_ref=96.0, noise_rel=0.01)
+        for r in rotors:
+            lat.add_turbine(**I.single_turbine(nx, ny, nz, diameter=D, hub=r["hub"], elements_per_blade=40,
+                                               tsr=r["tsr"], u_inf=u_hub, yaw=r["yaw"]))
+        lat.autotune(steps=5, cache=cache)
+        t = time.perf_counter()
+        if mode == "warm":
+            u0 = S.farm_initial_velocity(net, (nx, ny, nz), rotors, Uz, stride=4)
+            lat.init_fields(None, u0, None)
+            del u0
+        t_init = time.perf_counter() - t
+        steps = args.steps if mode == "cold" else args.steps // 2
+        wm = S.WindowMeans(lat, z=96, every=50, window=1000)
+        t = time.perf_counter()
+        wm.advance(steps)
+        t_run = time.perf_counter() - t
+        wms[mode] = wm
+        result[mode] = {"steps_run": steps, "run_s": t_run, "init_s": t_init, "mlups": nx * ny * nz * steps / t_run / 1e6}
+        lat.destroy()
+    ref, noise = S.converged_reference(wms["cold"], args.steps // 2)
+    tol = 2.0 * noise
+    for mode in ("cold", "warm"):
+        result[mode]["settled_at_step"] = S.settle_step(wms[mode], ref, tol)
+        result[mode]["window_errors"] = [round(e, 5) for e in S.window_errors(wms[mode], ref)[:20]]
+    line = {
+        "metric": METRIC, "value": result["cold"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "warmstart_farm_1024x384x192", "rotors": 9, "D": D, "inflow": "log law, 1% noise",
+                   "criterion": "first 1000-step window mean of hub-plane u_x within 2x the noise floor "
+                                "(relative L2) of the converged mean (second half of the cold run)",
+                   "noise_floor": noise, "tolerance": tol},
+        "surrogate": {"params": net.n_params, "train_samples": int(X.shape[0]), "final_mse": loss,
+                      "data_s": t_data, "train_s": t_train, "runs": len(runs)},
+        "cold": result["cold"], "warm": result["warm"],
+    }
+    net.destroy()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

@@ -81,6 +81,9 @@ typedef struct {
     int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 32 x 4;
                                 tile_x a multiple of 32, tile_x * tile_y <= 256 */
     int tile_z;              /* planes per CTA, each thread marching through them; 0 = default 1; <= 64 */
+    int staged;              /* 1: stage the 27 source rows of each 1-row tile in shared memory with
+                                asynchronous copies, persistent CTAs (needs tile_y = tile_z = 1 and nx a
+                                multiple of 4 (FP32) or 8 (16-bit)); 0 = direct loads */
 } lbm_config;
 
 typedef struct {
@@ -182,21 +185,22 @@ lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_s
 lbm_status lbm_get_step(lbm_ctx* ctx, long long* step);
 lbm_status lbm_set_step(lbm_ctx* ctx, long long step);
 
-/* CTA tile of the step kernel (see lbm_config.tile_*); changing it rebuilds the
- * work list.  Results do not depend on the tile.  INVALID_ARG for a bad shape. */
-lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z);
-lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z);
+/* CTA tile of the step kernel and the staged mode (see lbm_config.tile_* and
+ * staged); changing it rebuilds the work list.  Results do not depend on the
+ * tile.  INVALID_ARG for a bad shape. */
+lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z, int staged);
+lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z, int* staged);
 
 /* Autotuner: times the step kernel for a fixed set of CTA tiles (tile_x,
- * tile_y, tile_z) on the current state of every lattice of the batch
+ * tile_y, tile_z, staged) on the current state of every lattice of the batch
  * (steps_per_candidate timed launches each, after 3 untimed ones), restoring
  * the state (PDFs, rotor force boxes, step counter) after every candidate, and
  * applies the fastest.  cache_path (or NULL): a text file of
- * "<gpu/collision/storage/lattices key> tile_x tile_y tile_z ms" lines; a
+ * "<gpu/collision/storage/lattices key> tile_x tile_y tile_z staged ms" lines; a
  * matching line is applied without timing, a new result is appended.
  * tile_out receives the tile, best_ms its mean launch time.  The last
  * diagnostic result may be overwritten.  Synchronises. */
-lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[3],
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[4],
                         double* best_ms);
 
 /* Kernel timing: when enabled, lbm_step launches kernels one by one with CUDA
@@ -233,6 +237,36 @@ lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long
 lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, int nz, const double body_force[3],
                            const alm_turbine_desc* desc, long long step, float* elem_force, float* elem_pos,
                            double* loads, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Wake surrogate for warm starts.  Not part of the paper's method: a small
+ * multilayer perceptron n_in -> width (x n_hidden, GELU) -> n_out, trained on
+ * time-mean wake fields this solver produced, whose prediction initialises new
+ * runs (lbm_init_fields).  Weights: FP32 masters for the optimiser (Adam),
+ * BF16 copies in every product, FP32 accumulation.  Parameter vector layout
+ * (FP32): for each layer, W [out][in] row-major then b [out].  Host arrays
+ * are row-major [n][n_in] / [n][n_out].  Training is deterministic (fixed
+ * reduction orders, counter-based minibatch sampling). */
+typedef struct mlp_ctx mlp_ctx;
+
+/* width, n_in, n_out <= 128; 1 <= n_hidden <= 16.  Parameters start at zero. */
+lbm_status mlp_create(int n_in, int width, int n_hidden, int n_out, void* cuda_stream, mlp_ctx** out);
+void mlp_destroy(mlp_ctx* m);
+const char* mlp_last_error(const mlp_ctx* m);
+int mlp_num_params(const mlp_ctx* m);
+/* Set / read the FP32 parameters (set also resets the optimiser state). */
+lbm_status mlp_set_params(mlp_ctx* m, const float* params);
+lbm_status mlp_get_params(mlp_ctx* m, float* params);
+/* y [n][n_out] = network(x [n][n_in]).  Synchronises. */
+lbm_status mlp_forward(mlp_ctx* m, const float* x, int n, float* y);
+/* Mean squared error over all outputs of the batch and its gradient w.r.t.
+ * the parameters (grad may be NULL).  Synchronises. */
+lbm_status mlp_loss_grad(mlp_ctx* m, const float* x, const float* target, int n, double* loss, float* grad);
+/* Upload a training set, then run `steps` Adam steps (lr, beta = 0.9/0.999)
+ * on minibatches of `batch` rows drawn with splitmix64(seed, step*batch + k + 1)
+ * mod n.  last_loss: the MSE of the last minibatch (may be NULL). */
+lbm_status mlp_set_data(mlp_ctx* m, const float* x, const float* target, int n);
+lbm_status mlp_train(mlp_ctx* m, int steps, int batch, double lr, unsigned long long seed, double* last_loss);
 
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_gb300.so")
 
-SOURCES = ["lbm_kernels.cu", "lbm_abi.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_abi.cu", "lbm_noalloc.cu", "mlp_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -48,6 +48,8 @@ struct Batch {
     int diag_every = 0;
     long long host_step = 0;
     int tile_x = 32, tile_y = 4, tile_z = 1;
+    int staged = 0;        // rows staged in shared memory by persistent CTAs
+    unsigned staged_grid = 0;
     lbm_status status = LBM_OK;
     std::string err;
     bool dirty = true;
@@ -303,12 +305,13 @@ StepArgs step_args(Batch* b, int parity)
     a.diag_done = b->d_diag_done;
     a.diag_every = b->diag_every;
     a.tile_z = b->tile_z;
+    a.staged = b->staged;
     return a;
 }
 
 lbm_status launch_one(Batch* b, int parity)
 {
-    const dim3 grid(b->n_tiles), block(b->tile_x, b->tile_y);
+    const dim3 grid(b->staged ? std::min(b->n_tiles, b->staged_grid) : b->n_tiles), block(b->tile_x, b->tile_y);
     CK(launch_step(b->coll, b->store, grid, block, b->stream, step_args(b, parity)));
     return LBM_OK;
 }
@@ -369,6 +372,8 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     b->tile_x = cfgs[0].tile_x ? cfgs[0].tile_x : 32;
     b->tile_y = cfgs[0].tile_y ? cfgs[0].tile_y : 4;
     b->tile_z = cfgs[0].tile_z ? cfgs[0].tile_z : 1;
+    b->staged = 0;
+    const int want_staged = cfgs[0].staged;
     b->diag_every = cfgs[0].diag_every;
     b->inst.resize(n);
     lbm_status s = LBM_OK;
@@ -394,6 +399,13 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
         out[i]->b = b;
         out[i]->idx = i;
         b->refs++;
+    }
+    if (want_staged) {
+        const lbm_status st = lbm_set_tile(out[0], b->tile_x, b->tile_y, b->tile_z, 1);
+        if (st != LBM_OK) {
+            for (int i = 0; i < n; ++i) lbm_destroy(out[i]);
+            return st;
+        }
     }
     return LBM_OK;
 }
@@ -847,25 +859,50 @@ lbm_status lbm_set_step(lbm_ctx* ctx, long long step)
     return check_device_errors(b);
 }
 
-lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z)
+// Staged rows need one-row tiles and every lattice's nx a multiple of the
+// 16-byte chunk (4 FP32 or 8 16-bit values).
+static bool staged_ok(Batch* b, int tile_y, int tile_z)
+{
+    if (tile_y != 1 || tile_z != 1) return false;
+    const int chunk = b->store == STORE_FP32 ? 4 : 8;
+    for (auto& I : b->inst)
+        if (I.h.nx % chunk != 0) return false;
+    return true;
+}
+
+lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z, int staged)
 {
     ENTER(ctx);
     if (tile_x < 32 || tile_x % 32 != 0 || tile_y < 1 || tile_x * tile_y > 256 || tile_z < 1 || tile_z > 64)
         return fail(b, LBM_ERR_INVALID_ARG, "tile_x must be a multiple of 32, tile_x * tile_y <= 256, 1 <= tile_z <= 64",
                     false);
+    if (staged && !staged_ok(b, tile_y, tile_z))
+        return fail(b, LBM_ERR_INVALID_ARG, "staged rows need tile_y = tile_z = 1 and nx a multiple of 16 bytes", false);
+    unsigned grid = 0;
+    if (staged) {
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int per_sm = staged_blocks_per_sm(b->coll, b->store, tile_x);
+        if (per_sm < 1) return fail(b, LBM_ERR_INVALID_ARG, "staged tile does not fit on an SM", false);
+        grid = (unsigned)(per_sm * sms);
+    }
     b->tile_x = tile_x;
     b->tile_y = tile_y;
     b->tile_z = tile_z;
+    b->staged = staged ? 1 : 0;
+    b->staged_grid = grid;
     b->dirty = true;
     return sync_descriptors(b);
 }
 
-lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z)
+lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z, int* staged)
 {
     ENTER(ctx);
     if (tile_x) *tile_x = b->tile_x;
     if (tile_y) *tile_y = b->tile_y;
     if (tile_z) *tile_z = b->tile_z;
+    if (staged) *staged = b->staged;
     return LBM_OK;
 }
 
@@ -933,7 +970,7 @@ std::string tune_key(Batch* b)
 
 }  // namespace
 
-lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[3],
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[4],
                         double* best_ms)
 {
     ENTER(ctx);
@@ -942,28 +979,30 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
     if (cache_path) {
         if (FILE* fp = std::fopen(cache_path, "r")) {
             char kbuf[1024];
-            int tx, ty, tz, hx = 0, hy = 0, hz = 0;
+            int tx, ty, tz, st, hx = 0, hy = 0, hz = 0, hs = 0;
             double ms, hms = 0.0;
             bool hit = false;
-            while (std::fscanf(fp, "%1023s %d %d %d %lf", kbuf, &tx, &ty, &tz, &ms) == 5)
+            while (std::fscanf(fp, "%1023s %d %d %d %d %lf", kbuf, &tx, &ty, &tz, &st, &ms) == 6)
                 if (key == kbuf) {
                     hit = true;
                     hx = tx;
                     hy = ty;
                     hz = tz;
+                    hs = st;
                     hms = ms;
                 }
             std::fclose(fp);
             if (hit) {
-                if (tile_out) { tile_out[0] = hx; tile_out[1] = hy; tile_out[2] = hz; }
+                if (tile_out) { tile_out[0] = hx; tile_out[1] = hy; tile_out[2] = hz; tile_out[3] = hs; }
                 if (best_ms) *best_ms = hms;
-                return lbm_set_tile(ctx, hx, hy, hz);
+                return lbm_set_tile(ctx, hx, hy, hz, hs);
             }
         }
     }
-    static const int cand[][3] = {{32, 4, 1}, {32, 2, 1}, {32, 8, 1}, {64, 2, 1}, {64, 1, 1}, {128, 1, 1},
-                                  {32, 4, 2}, {32, 4, 4}, {32, 2, 4}, {32, 2, 8}, {64, 2, 4}, {32, 8, 2},
-                                  {64, 4, 2}, {128, 1, 4}, {32, 4, 8}};
+    // tile_x, tile_y, tile_z, staged
+    static const int cand[][4] = {{32, 4, 1, 0}, {32, 2, 1, 0}, {32, 8, 1, 0}, {64, 2, 1, 0}, {64, 1, 1, 0},
+                                  {128, 1, 1, 0}, {32, 4, 2, 0}, {32, 4, 4, 0}, {32, 2, 4, 0}, {32, 2, 8, 0},
+                                  {64, 2, 4, 0}, {32, 4, 8, 0}, {64, 1, 1, 1}, {128, 1, 1, 1}, {256, 1, 1, 1}};
     const long long step0 = b->host_step;
     const bool prof = b->profiling;
     Snapshot S;
@@ -972,10 +1011,13 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
     int best = -1;
     double best_t = 1e300;
     for (int c = 0; s == LBM_OK && c < (int)(sizeof cand / sizeof cand[0]); ++c) {
-        b->tile_x = cand[c][0];
-        b->tile_y = cand[c][1];
-        b->tile_z = cand[c][2];
-        b->dirty = true;
+        if (cand[c][3] && !staged_ok(b, cand[c][1], cand[c][2])) continue;
+        s = lbm_set_tile(ctx, cand[c][0], cand[c][1], cand[c][2], cand[c][3]);
+        if (s == LBM_ERR_INVALID_ARG) {  // does not fit: skip the candidate
+            s = LBM_OK;
+            continue;
+        }
+        if (s != LBM_OK) break;
         s = snapshot_restore(b, S, step0);
         if (s != LBM_OK) break;
         b->profiling = false;
@@ -999,22 +1041,17 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
     b->ev_used = 0;
     b->prof_ms = 0.0;
     b->prof_n = 0;
-    if (best >= 0) {
-        b->tile_x = cand[best][0];
-        b->tile_y = cand[best][1];
-        b->tile_z = cand[best][2];
-        b->dirty = true;
-    }
+    if (best >= 0 && s == LBM_OK) s = lbm_set_tile(ctx, cand[best][0], cand[best][1], cand[best][2], cand[best][3]);
     if (!S.f.empty() && s == LBM_OK) s = snapshot_restore(b, S, step0);
     for (void* p : S.f) dfree(b, p);
     for (float* p : S.box) dfree(b, p);
     if (s != LBM_OK) return s;
     if (best < 0) return fail(b, LBM_ERR_STATE, "no tile candidate ran");
-    if (tile_out) { tile_out[0] = b->tile_x; tile_out[1] = b->tile_y; tile_out[2] = b->tile_z; }
+    if (tile_out) { tile_out[0] = b->tile_x; tile_out[1] = b->tile_y; tile_out[2] = b->tile_z; tile_out[3] = b->staged; }
     if (best_ms) *best_ms = best_t;
     if (cache_path)
         if (FILE* fp = std::fopen(cache_path, "a")) {
-            std::fprintf(fp, "%s %d %d %d %.9g\n", key.c_str(), b->tile_x, b->tile_y, b->tile_z, best_t);
+            std::fprintf(fp, "%s %d %d %d %d %.9g\n", key.c_str(), b->tile_x, b->tile_y, b->tile_z, b->staged, best_t);
             std::fclose(fp);
         }
     return LBM_OK;

@@ -88,6 +88,7 @@ struct StepArgs {
     unsigned int* diag_done;            // CTA completion counter, used on diagnostic steps only
     int diag_every;                     // diagnostic period shared by the batch (0 = off)
     int tile_z;                         // planes per CTA (1: no marching)
+    int staged;                         // rows staged in shared memory by persistent CTAs
 };
 
 // Work-list entry: bit 63 rotor tile, bits 48..62 instance, 32..47 z, 16..31 y0, 0..15 x0.
@@ -101,6 +102,7 @@ __host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0,
 // Host-side launchers (lbm_kernels.cu).
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a);
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
+int staged_blocks_per_sm(int coll, int store, int width);
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);
 cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const float* drho,
                         const float* u, const float* fneq, int parity, int inflow_mean, cudaStream_t s);

@@ -44,6 +44,10 @@ template <> struct Io<__half> {
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+
 // ------------------------------------------------------------------ inflow
 
 // splitmix64 (Steele, Lea, Flood 2014): k-th output of the generator started at `seed`.
@@ -905,6 +909,294 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
     }
 }
 
+// ------------------------------------------------------------------ staged step
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Elements per 16-byte chunk: the halo kept on each side of a staged row.
+template <typename T> __host__ __device__ constexpr int halo_of() { return 16 / (int)sizeof(T); }
+
+// Issue the asynchronous copies of one row segment (tile with tile_y = 1):
+// for each direction q, source row (y - c_y, z - c_z) (wrapped or clamped as
+// in load_cell), elements [x0 - H, x0 + W + H) clipped to the row, into
+// stage[q][x - x0 + H].  nx is a multiple of H, so every chunk is aligned.
+template <typename T>
+__device__ __forceinline__ void stage_issue(const DevDomain* D, const T* __restrict__ src, int x0, int y, int z, int W,
+                                            T* stage)
+{
+    constexpr int H = halo_of<T>();
+    const int nx = D->nx, ny = D->ny, nz = D->nz;
+    const int by = D->bc[1], bz = D->bc[2];
+    int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
+    else { ym = max(ym, 0); yp = min(yp, ny - 1); }
+    if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
+    else { zm = max(zm, 0); zp = min(zp, nz - 1); }
+    const int lo = max(x0 - H, 0), hi = min(x0 + W + H, nx);
+    const int nch = (hi - lo) / H;
+    const int rowlen = W + 2 * H;
+    const unsigned uN = (unsigned)D->N;
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    // one warp per direction q, one lane per 16-byte chunk of its row
+    for (int q = threadIdx.x >> 5; q < 27; q += nwarps) {
+        const int j = (q / 3) % 3, kk = q / 9;
+        const int ys = j == 0 ? yp : (j == 1 ? y : ym);
+        const int zs = kk == 0 ? zp : (kk == 1 ? z : zm);
+        const T* row = src + ((unsigned)q * uN + ((unsigned)zs * (unsigned)ny + (unsigned)ys) * (unsigned)nx);
+        T* dst = stage + q * rowlen + (lo - x0 + H);
+        for (int c = lane; c < nch; c += 32) cp_async16(dst + c * H, row + lo + c * H);
+    }
+    cp_async_commit();
+}
+
+// k_step with the source rows staged in shared memory: persistent CTAs walk
+// the work list (one row segment of blockDim.x cells per entry) and copy the
+// next segment's 27 rows asynchronously while the current one collides, so
+// the loads in flight cost no registers.  Same arithmetic, same results as
+// k_step.
+template <int COLL, typename T>
+__global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
+{
+    constexpr int H = halo_of<T>();
+    constexpr int kCull = 128;
+    extern __shared__ __align__(16) unsigned char stage_raw[];
+    __shared__ double s_red[8][4];
+    __shared__ int s_flag;
+    __shared__ float4 s_pos[kCull], s_frc[kCull];
+    __shared__ int s_tag[kCull];
+    __shared__ int s_cnt[8];
+    const int W = blockDim.x;
+    const int rowlen = W + 2 * H;
+    T* stages[2] = {(T*)stage_raw, (T*)stage_raw + 27 * rowlen};
+    const int tid = threadIdx.x;
+    const int par = A.parity;
+    const long long step = __ldcg(A.step_slot + par);
+    if (blockIdx.x == 0 && tid == 0) A.step_slot[par ^ 1] = step + 1;
+    const bool diag = A.diag_every > 0 && (step % A.diag_every) == 0;
+    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+
+    unsigned it = blockIdx.x;
+    if (it < A.n_tiles) {
+        const unsigned long long t0 = A.tiles[it];
+        const DevDomain* D0 = A.dom + ((t0 >> 48) & 0x7FFF);
+        stage_issue<T>(D0, (const T*)D0->f[par], (int)(t0 & 0xFFFF), (int)((t0 >> 16) & 0xFFFF),
+                       (int)((t0 >> 32) & 0xFFFF), W, stages[0]);
+    }
+    for (int k = 0; it < A.n_tiles; ++k, it += gridDim.x) {
+        const unsigned long long tile = A.tiles[it];
+        const bool rotor_tile = (tile >> 63) != 0;
+        const DevDomain* D = A.dom + ((tile >> 48) & 0x7FFF);
+        const int z = (int)((tile >> 32) & 0xFFFF);
+        const int y = (int)((tile >> 16) & 0xFFFF);
+        const int x0 = (int)(tile & 0xFFFF);
+        const int x = x0 + tid;
+        const int nx = D->nx, ny = D->ny, nz = D->nz;
+        const unsigned uN = (unsigned)D->N;
+        const T* __restrict__ src = (const T*)D->f[par];
+        T* __restrict__ dst = (T*)D->f[par ^ 1];
+        const T* st = stages[k & 1];
+        cp_async_wait_all();
+        __syncthreads();
+        // next segment's rows go to the other buffer (read in the previous iteration)
+        const unsigned nit = it + gridDim.x;
+        if (nit < A.n_tiles) {
+            const unsigned long long tn = A.tiles[nit];
+            const DevDomain* Dn = A.dom + ((tn >> 48) & 0x7FFF);
+            stage_issue<T>(Dn, (const T*)Dn->f[par], (int)(tn & 0xFFFF), (int)((tn >> 16) & 0xFFFF),
+                           (int)((tn >> 32) & 0xFFFF), W, stages[(k + 1) & 1]);
+        }
+        // rotor segment: cull the blade elements reaching it
+        int n_cull = -1;
+        if (rotor_tile) {
+            const float tx0 = (float)x0, tx1 = (float)(x0 + W - 1), fy = (float)y, fz = (float)z;
+            const float4* P = D->el_pos[step & 1];
+            const float4* Fe = D->el_force[step & 1];
+            const int lane = tid & 31, warp = tid >> 5, nwarps = W >> 5;
+            int total = 0;
+            for (int base = 0; base < D->n_el; base += W) {
+                const int e = base + tid;
+                bool keep = false;
+                float4 pe = make_float4(0.f, 0.f, 0.f, 0.f);
+                int t = 0;
+                if (e < D->n_el) {
+                    pe = __ldg(P + e);
+                    while (t + 1 < D->n_turb && D->turb[t + 1].el_offset <= e) ++t;
+                    const float cut = D->turb[t].cut;
+                    keep = pe.x + cut >= tx0 && pe.x - cut <= tx1 && fabsf(pe.y - fy) <= cut && fabsf(pe.z - fz) <= cut;
+                }
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+                if (lane == 0) s_cnt[warp] = __popc(m);
+                __syncthreads();
+                int off = total, chunk = 0;
+                for (int w = 0; w < nwarps; ++w) {
+                    if (w < warp) off += s_cnt[w];
+                    chunk += s_cnt[w];
+                }
+                const int pos = off + __popc(m & ((1u << lane) - 1u));
+                if (keep && pos < kCull) {
+                    s_pos[pos] = pe;
+                    s_frc[pos] = __ldg(Fe + e);
+                    s_tag[pos] = t;
+                }
+                total += chunk;
+                __syncthreads();
+            }
+            n_cull = total <= kCull ? total : -1;
+        }
+        if (x < nx) {
+            float h[27];
+            const int bx = D->bc[0], by = D->bc[1], bz = D->bc[2];
+            // staged rows: x - c_x at column tid + H - c_x; periodic x wraps past the row ends (direct loads)
+            const bool wrap_lo = bx == BC_PERIODIC && x == 0, wrap_hi = bx == BC_PERIODIC && x == nx - 1;
+            const int cm = (x == 0) ? tid + H : tid + H - 1;          // source x - 1 (clamped at 0)
+            const int cp = (x == nx - 1) ? tid + H : tid + H + 1;     // source x + 1 (clamped at nx - 1)
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int cxq = q % 3 - 1;
+                const int col = cxq == 1 ? cm : (cxq == 0 ? tid + H : cp);
+                h[q] = to_float(st[q * rowlen + col]);
+            }
+            if (wrap_lo || wrap_hi) {
+                int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+                if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
+                else { ym = max(ym, 0); yp = min(yp, ny - 1); }
+                if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
+                else { zm = max(zm, 0); zp = min(zp, nz - 1); }
+                const unsigned ys3[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+                const unsigned zs3[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+                const unsigned xw = wrap_lo ? (unsigned)(nx - 1) : 0u;
+                const int cw = wrap_lo ? 2 : 0;  // the c_x that reads across the wrap
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    if (q % 3 != cw) continue;
+                    const unsigned row = (zs3[q / 9] * (unsigned)ny + ys3[(q / 3) % 3]) * (unsigned)nx;
+                    h[q] = Io<T>::ld(src + ((unsigned)q * uN + row + xw));
+                }
+            }
+            // inlet and wall rules as in load_cell
+            if (bx == BC_INOUT && x == 0) {
+                int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+                if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
+                else { ym = max(ym, 0); yp = min(yp, ny - 1); }
+                if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
+                else { zm = max(zm, 0); zp = min(zp, nz - 1); }
+                const int ys3[3] = {yp, y, ym}, zs3[3] = {zp, z, zm};
+                const float* ub = D->inflow_u[step & 1];
+                const int plane = ny * nz;
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int q = kk * 9 + j * 3 + 2;
+                        const bool wall = (by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
+                                          (bz == BC_NOSLIP && ((kk == 2 && z == 0) || (kk == 0 && z == nz - 1)));
+                        if (!wall) {
+                            const int col = zs3[kk] * ny + ys3[j];
+                            h[q] = feq_offset_one(q, ub[col], ub[plane + col], ub[2 * plane + col]);
+                        }
+                    }
+            }
+            const bool walls = ((bx == BC_NOSLIP || bx == BC_FREESLIP) && (x == 0 || x == nx - 1)) ||
+                               ((by == BC_NOSLIP || by == BC_FREESLIP) && (y == 0 || y == ny - 1)) ||
+                               ((bz == BC_NOSLIP || bz == BC_FREESLIP) && (z == 0 || z == nz - 1));
+            if (walls) {
+                float hl[27];
+#pragma unroll
+                for (int q = 0; q < 27; ++q) hl[q] = h[q];
+                boundary_patch<T>(D, src, x, y, z, step, hl);
+#pragma unroll
+                for (int q = 0; q < 27; ++q) h[q] = hl[q];
+            }
+            if (bx == BC_INOUT && x == 0) {
+                float u[3];
+                inflow_velocity(D, step + 1, y, z, u);
+                float* ub = D->inflow_u[(step + 1) & 1];
+                const int plane = ny * nz, col = z * ny + y;
+                ub[col] = u[0];
+                ub[plane + col] = u[1];
+                ub[2 * plane + col] = u[2];
+            }
+            float F[3] = {D->body[0], D->body[1], D->body[2]};
+            if (rotor_tile) rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
+            float m, jx, jy, jz;
+            if (COLL == COLL_CUMULANT)
+                collide_cumulant(h, F[0], F[1], F[2], D->omega, m, jx, jy, jz);
+            else
+                collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, m, jx, jy, jz);
+            o_m += m;
+            o_jx += jx;
+            o_jy += jy;
+            o_jz += jz;
+            const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
+        }
+        // diagnostic step: this segment's FP64 sums go to its own lattice
+        if (diag) {
+            double v[4] = {o_m, o_jx, o_jy, o_jz};
+            o_m = o_jx = o_jy = o_jz = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) v[kk] += __shfl_xor_sync(0xFFFFFFFFu, v[kk], o);
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) s_red[tid >> 5][kk] = v[kk];
+            __syncthreads();
+            if (tid == 0)
+                for (int kk = 0; kk < 4; ++kk) {
+                    double sum = 0.0;
+                    for (int w = 0; w < (W >> 5); ++w) sum += s_red[w][kk];
+                    atomicAdd(D->diag_acc + kk, sum);
+                }
+            __syncthreads();
+        }
+        // last rotor segment of this lattice: actuator line of the next step
+        if (rotor_tile) {
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const unsigned prev = atomicAdd(D->rotor_counter, 1u);
+                s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                alm_compute<T>(D, dst, step + 1);
+                if (tid == 0) *D->rotor_counter = 0u;
+            }
+        }
+    }
+    cp_async_wait_all();
+    // diagnostic step: the last CTA closes the sums of every lattice
+    if (diag && tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(A.diag_done, 1u);
+        if (prev == gridDim.x - 1u) {
+            __threadfence();
+            for (int i = 0; i < A.n_inst; ++i) {
+                const DevDomain* Di = A.dom + i;
+                bool finite = true;
+                for (int kk = 0; kk < 4; ++kk) {
+                    const double sum = __ldcg(Di->diag_acc + kk);
+                    Di->diag_res[kk] = sum;
+                    Di->diag_acc[kk] = 0.0;
+                    if (!isfinite(sum)) finite = false;
+                }
+                Di->diag_res[4] = (double)step;
+                if (!finite) atomicOr(Di->err, ERR_NONFINITE);
+            }
+            *A.diag_done = 0u;
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_alm(const DevDomain* dom, int parity, long long step)
 {
@@ -1034,11 +1326,17 @@ static int grid_for(long long n, int block)
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a)
 {
     const bool march = a.tile_z > 1;
-#define LBM_STEP_CASE(C, S, T)                                      \
-    if (coll == C && store == S) {                                  \
-        if (march) k_step<C, T, true><<<grid, block, 0, s>>>(a);    \
-        else k_step<C, T, false><<<grid, block, 0, s>>>(a);         \
-        return cudaGetLastError();                                  \
+#define LBM_STEP_CASE(C, S, T)                                                                        \
+    if (coll == C && store == S) {                                                                    \
+        if (a.staged) {                                                                               \
+            const size_t smem = 2 * 27 * (size_t)(block.x + 2 * halo_of<T>()) * sizeof(T);            \
+            k_step_staged<C, T><<<grid, block, smem, s>>>(a);                                         \
+        } else if (march) {                                                                           \
+            k_step<C, T, true><<<grid, block, 0, s>>>(a);                                             \
+        } else {                                                                                      \
+            k_step<C, T, false><<<grid, block, 0, s>>>(a);                                            \
+        }                                                                                             \
+        return cudaGetLastError();                                                                    \
     }
     LBM_STEP_CASE(COLL_CUMULANT, STORE_FP32, float)
     LBM_STEP_CASE(COLL_CUMULANT, STORE_BF16, __nv_bfloat16)
@@ -1048,6 +1346,31 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
     LBM_STEP_CASE(COLL_SRT_SMAG, STORE_FP16, __half)
 #undef LBM_STEP_CASE
     return cudaErrorInvalidValue;
+}
+
+// Resident CTAs per SM of the staged kernel for a block width (persistent grid),
+// raising its dynamic shared memory limit when needed.
+int staged_blocks_per_sm(int coll, int store, int width)
+{
+    int n = 0;
+#define LBM_OCC_CASE(C, S, T)                                                                                    \
+    if (coll == C && store == S) {                                                                               \
+        const size_t smem = 2 * 27 * (size_t)(width + 2 * halo_of<T>()) * sizeof(T);                            \
+        if (cudaFuncSetAttribute(k_step_staged<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != \
+            cudaSuccess)                                                                                         \
+            return 0;                                                                                            \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_staged<C, T>, width, smem) != cudaSuccess)  \
+            return 0;                                                                                            \
+        return n;                                                                                                \
+    }
+    LBM_OCC_CASE(COLL_CUMULANT, STORE_FP32, float)
+    LBM_OCC_CASE(COLL_CUMULANT, STORE_BF16, __nv_bfloat16)
+    LBM_OCC_CASE(COLL_CUMULANT, STORE_FP16, __half)
+    LBM_OCC_CASE(COLL_SRT_SMAG, STORE_FP32, float)
+    LBM_OCC_CASE(COLL_SRT_SMAG, STORE_BF16, __nv_bfloat16)
+    LBM_OCC_CASE(COLL_SRT_SMAG, STORE_FP16, __half)
+#undef LBM_OCC_CASE
+    return n;
 }
 
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s)

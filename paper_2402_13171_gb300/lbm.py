@@ -44,6 +44,7 @@ class LbmConfig(ctypes.Structure):
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
+        ("staged", ctypes.c_int),
     ]
 
 
@@ -98,12 +99,12 @@ def load():
         "lbm_set_profiling": [ctypes.c_void_p, ctypes.c_int],
         "lbm_get_kernel_time": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_get_traffic_model": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
-        "lbm_set_tile": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "lbm_set_tile": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "lbm_probe": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, _dp, _dp],
         "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(ctypes.c_double)],
         "lbm_get_tile": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                         ctypes.POINTER(ctypes.c_int)],
+                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -163,6 +164,7 @@ def make_config(nx, ny, nz, collision="cumulant", nu=0.01, smag_c=0.0, storage="
         c.dev_free = allocator.free_cb
     c.tile_x, c.tile_y = int(tile[0]), int(tile[1])
     c.tile_z = int(tile[2]) if len(tile) > 2 else 0
+    c.staged = int(tile[3]) if len(tile) > 3 else 0
     return c
 
 
@@ -315,17 +317,18 @@ class Lattice:
         self._call("lbm_get_kernel_time", ctypes.byref(ms), ctypes.byref(n))
         return ms.value, n.value
 
-    def set_tile(self, tx, ty, tz=1):
-        self._call("lbm_set_tile", int(tx), int(ty), int(tz))
+    def set_tile(self, tx, ty, tz=1, staged=0):
+        self._call("lbm_set_tile", int(tx), int(ty), int(tz), int(staged))
 
     def autotune(self, steps=20, cache=None):
-        out = (ctypes.c_int * 3)()
+        out = (ctypes.c_int * 4)()
         ms = ctypes.c_double()
         self._call("lbm_autotune", int(steps), None if cache is None else str(cache).encode(), out, ctypes.byref(ms))
         return tuple(out), ms.value
 
     def tile(self):
-        v = [ctypes.c_int() for _ in range(3)]
+        """(tile_x, tile_y, tile_z, staged)."""
+        v = [ctypes.c_int() for _ in range(4)]
         self._call("lbm_get_tile", *[ctypes.byref(a) for a in v])
         return tuple(a.value for a in v)
 

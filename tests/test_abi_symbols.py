@@ -46,7 +46,7 @@ def test_config_struct_matches_header_layout():
     body = hdr[hdr.index("typedef struct {\n    int nx, ny, nz;"):]
     body = body[:body.index("} lbm_config;")]
     order = ["nx", "collision", "nu", "smag_c", "storage", "bc", "body_force", "seed", "diag_every", "cuda_stream",
-             "dev_alloc", "dev_free", "alloc_user", "tile_x", "tile_z"]
+             "dev_alloc", "dev_free", "alloc_user", "tile_x", "tile_z", "staged"]
     pos = [body.index(k) for k in order]
     assert pos == sorted(pos)
     fields = [f[0] for f in lbm.LbmConfig._fields_]

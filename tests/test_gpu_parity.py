@@ -193,6 +193,50 @@ def test_tile_shapes_agree(tile):
     np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
 
 
+@pytest.mark.parametrize("bc", [("periodic", "periodic", "periodic"), ("inout", "periodic", "freeslip"),
+                                ("noslip", "noslip", "periodic"), ("freeslip", "freeslip", "noslip")])
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_staged_rows_match_direct_loads(bc, storage):
+    """Rows staged in shared memory by persistent CTAs give bitwise the same
+    step as direct loads: wrap lanes, a ragged last segment (nx = 104 with
+    64-wide segments), inlet/outlet and wall faces, a rotor, diagnostics."""
+    nx = 104
+    dom, turb = I.single_turbine_case(nx, 40, 40, diameter=16.0, elements_per_blade=8, seed=91)
+    dom["bc"] = bc
+    rho, u, fneq = I.random_state(nx, 40, 40, seed=8, u_mean=(0.04, 0.0, 0.0), du=0.01)
+    ga, _ = setup_pair(dom, [turb], rho=rho, u=u, fneq=fneq, inflow=bc[0] == "inout", storage=storage, diag_every=3)
+    gb, _ = setup_pair(dom, [turb], rho=rho, u=u, fneq=fneq, inflow=bc[0] == "inout", storage=storage, diag_every=3,
+                       tile=(64, 1, 1, 1))
+    assert gb.tile() == (64, 1, 1, 1)
+    ga.step(7)
+    gb.step(7)
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    assert ga.loads(0) == gb.loads(0)
+    da, _ = ga.diagnostics()
+    db, _ = gb.diagnostics()
+    np.testing.assert_allclose(da, db, rtol=0, atol=1e-9)
+
+
+def test_staged_batch_matches_direct():
+    from paper_2402_13171_gb300 import lbm
+    cases = [I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=s) for s in (1, 2)]
+    cases.append(I.single_turbine_case(96, 48, 44, diameter=20.0, elements_per_blade=6, seed=3))
+    runs = []
+    for tile in ((32, 4, 1, 0), (128, 1, 1, 1)):
+        cfgs = [dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], nu=d["nu"], bc=d["bc"], seed=d["seed"], tile=tile,
+                     diag_every=4) for d, _ in cases]
+        lat = lbm.batch_create(cfgs)
+        for L, (d, t) in zip(lat, cases):
+            L.set_inflow(u_ref=d["u_ref"], noise_rel=d["noise_rel"])
+            L.add_turbine(**t)
+        lat[0].step(9)
+        runs.append([(L.pdfs(), L.loads(0), L.diagnostics()[0]) for L in lat])
+    for (fa, la, da), (fb, lb, db) in zip(*runs):
+        np.testing.assert_array_equal(fa, fb)
+        assert la == lb
+        np.testing.assert_allclose(da, db, rtol=0, atol=1e-9)
+
+
 def test_autotune_keeps_state_and_results():
     """The tuner times tile candidates on the live state and restores it: the
     run continues exactly as an untuned one."""
