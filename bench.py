@@ -14,6 +14,7 @@ the host cores instead (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -28,6 +29,7 @@ if ROOT not in sys.path:
 
 METRIC = "MLUPS & % HBM roofline per GB300 (fused LBM+ALM step) vs plain FP32 at stated accuracy"
 WORKLOAD = "single_turbine_256x128x128"
+DIAG_EVERY = 100  # FP64 mass/momentum sums fused into every 100th step
 
 
 def parse_args():
@@ -52,6 +54,30 @@ def parse_args():
 
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# DRAM bytes per k_step launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of `bench.py --tile <tile> --steps 20 --warmup 3`, keyed
+# by (workload, storage, collision, tile).  They hold for the kernel source
+# whose SHA-256 is recorded and are reported as null once it changes.
+NCU_TRAFFIC = {
+    "kernel_sha256": "",
+    "bytes": {},
+}
+
+
+def kernel_source_sha256():
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cu", "lbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_2402_13171_gb300", "csrc", f), "rb") as fp:
+            h.update(fp.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload, storage, collision, tile):
+    if NCU_TRAFFIC["kernel_sha256"] != kernel_source_sha256():
+        return None
+    return NCU_TRAFFIC["bytes"].get((workload, storage, collision, tile))
 
 
 def load_peaks():
@@ -212,7 +238,7 @@ def run_ours(args):
         dom["collision"] = args.collision
         lat = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], device=local, collision=args.collision,
                                  nu=dom["nu"], smag_c=dom["smag_c"], storage=args.storage, bc=dom["bc"],
-                                 seed=dom["seed"], tile=tile)
+                                 seed=dom["seed"], tile=tile, diag_every=DIAG_EVERY)
         lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
         lat.add_turbine(**turb)
         lattices = [lat]
@@ -221,7 +247,8 @@ def run_ours(args):
     else:
         cases = I.batch_instances(16)
         cfgs = [dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], collision=args.collision, nu=d["nu"], smag_c=d["smag_c"],
-                     storage=args.storage, bc=d["bc"], seed=d["seed"], tile=tile) for d, _ in cases]
+                     storage=args.storage, bc=d["bc"], seed=d["seed"], tile=tile, diag_every=DIAG_EVERY)
+                for d, _ in cases]
         lattices = lbm.batch_create(cfgs, device=local)
         for L, (d, t) in zip(lattices, cases):
             L.set_inflow(u_ref=d["u_ref"], noise_rel=d["noise_rel"])
@@ -264,6 +291,7 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     achieved = bytes_per_cell * cells / (kernel_ms * 1e-3) / 1e9
     thrust, torque = lat.loads(0)
+    diag_sums, diag_step = lat.diagnostics()
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -313,11 +341,12 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "cells": cells, "storage": args.storage, "collision": args.collision,
                        **extra,
-                       "tile": tile_used, "tuned": args.tile == "auto",
+                       "tile": tile_used, "tuned": args.tile == "auto", "diag_every": DIAG_EVERY,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"no flush: PDF arrays {2 * bytes_per_cell / 2 * cells / 1e6:.0f} MB > 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": measured_traffic(workload, args.storage, args.collision, tile_used),
                          "kernel": "k_step (fused stream-collide + in-kernel ALM)",
                          "bytes_per_cell": bytes_per_cell, "kernel_ms": kernel_ms, "peak_kind": peak_kind},
             "e2e": e2e,
@@ -326,6 +355,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "accuracy": {"max_du_vs_fp64_oracle": acc, "case": "48x32x32 rotor, 50 steps"} if acc is not None else None,
             "loads": {"thrust": thrust, "torque": torque},
+            "diagnostics": {"step": diag_step, "sum_drho": diag_sums[0], "momentum": list(diag_sums[1:])},
         }
         print(json.dumps(line), flush=True)
     for L in lattices:
@@ -422,10 +452,11 @@ def run_warmstart(args):
     u(z) = 0.05 ln(z_c/0.1)/ln(96/0.1) with 1 % noise, free-slip top and
     bottom, periodic y.  The surrogate (6 -> 4 x 128 GELU -> 3, BF16 weights)
     is trained on the mean wakes of 64 single-rotor runs of this solver.  The
-    farm runs from the inflow profile (cold, --steps steps; its second half
-    gives the converged mean and its noise floor) and from the surrogate's
-    superposed wakes (warm, --steps/2); each settles at the first 1000-step
-    window of hub-plane u_x within twice the noise floor of the converged mean."""
+    farm runs --steps steps from the inflow profile (cold) and from the
+    surrogate's superposed wakes (warm); the second halves of both give the
+    converged mean of hub-plane u_x and its noise floor (median distance of a
+    1000-step window mean to it); each run settles at its first window within
+    k times the noise floor, k = 2, 3, 4."""
     import numpy as np
     import torch
 
@@ -467,27 +498,26 @@ def run_warmstart(args):
             lat.init_fields(None, u0, None)
             del u0
         t_init = time.perf_counter() - t
-        steps = args.steps if mode == "cold" else args.steps // 2
         wm = S.WindowMeans(lat, z=96, every=50, window=1000)
         t = time.perf_counter()
-        wm.advance(steps)
+        wm.advance(args.steps)
         t_run = time.perf_counter() - t
         wms[mode] = wm
-        result[mode] = {"steps_run": steps, "run_s": t_run, "init_s": t_init, "mlups": nx * ny * nz * steps / t_run / 1e6}
+        result[mode] = {"steps_run": args.steps, "run_s": t_run, "init_s": t_init,
+                        "mlups": nx * ny * nz * args.steps / t_run / 1e6}
         lat.destroy()
-    ref, noise = S.converged_reference(wms["cold"], args.steps // 2)
-    tol = 2.0 * noise
+    ref, noise = S.converged_reference([wms["cold"], wms["warm"]], args.steps // 2)
     for mode in ("cold", "warm"):
-        result[mode]["settled_at_step"] = S.settle_step(wms[mode], ref, tol)
-        result[mode]["window_errors"] = [round(e, 5) for e in S.window_errors(wms[mode], ref)[:20]]
+        result[mode]["settled_at_step"] = {f"{k}x_noise": S.settle_step(wms[mode], ref, k * noise) for k in (2, 3, 4)}
+        result[mode]["window_errors"] = [round(e, 4) for e in S.window_errors(wms[mode], ref)]
     line = {
         "metric": METRIC, "value": result["cold"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
         "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "warmstart_farm_1024x384x192", "rotors": 9, "D": D, "inflow": "log law, 1% noise",
-                   "criterion": "first 1000-step window mean of hub-plane u_x within 2x the noise floor "
-                                "(relative L2) of the converged mean (second half of the cold run)",
-                   "noise_floor": noise, "tolerance": tol},
+                   "criterion": "first 1000-step window mean of hub-plane u_x within k x the noise floor "
+                                "(relative L2) of the converged mean (second halves of both runs), k = 2, 3, 4",
+                   "noise_floor": noise},
         "surrogate": {"params": net.n_params, "train_samples": int(X.shape[0]), "final_mse": loss,
                       "data_s": t_data, "train_s": t_train, "runs": len(runs)},
         "cold": result["cold"], "warm": result["warm"],

@@ -44,7 +44,9 @@ struct Batch {
     size_t tiles_cap = 0;
     unsigned n_tiles = 0;
     long long* d_step = nullptr;          // two slots: step n lives in slot [n & 1]
+    int* d_diag_flag = nullptr;           // two slots: 1 if step n is a diagnostic step
     unsigned int* d_diag_done = nullptr;
+    int host_diag_flag = 0;
     int diag_every = 0;
     long long host_step = 0;
     int tile_x = 32, tile_y = 4, tile_z = 1;
@@ -302,11 +304,25 @@ StepArgs step_args(Batch* b, int parity)
     a.n_inst = (int)b->inst.size();
     a.parity = parity;
     a.step_slot = b->d_step;
+    a.diag_flag = b->d_diag_flag;
     a.diag_done = b->d_diag_done;
     a.diag_every = b->diag_every;
     a.tile_z = b->tile_z;
     a.staged = b->staged;
     return a;
+}
+
+// Step counter and diagnostic flag of host_step into their device slots.
+cudaError_t write_step_slot(Batch* b)
+{
+    const int slot = (int)(b->host_step & 1);
+    b->host_diag_flag = b->diag_every > 0 && b->host_step % b->diag_every == 0;
+    cudaError_t e = cudaMemcpyAsync(b->d_step + slot, &b->host_step, sizeof(long long), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_diag_flag + slot, &b->host_diag_flag, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->stream) e = cudaStreamSynchronize(b->stream);
+    return e;
 }
 
 lbm_status launch_one(Batch* b, int parity)
@@ -385,7 +401,9 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
         else {
             b->d_step = (long long*)sc;
             b->d_diag_done = (unsigned int*)((char*)sc + 16);
-            if (cudaMemsetAsync(sc, 0, 64, b->stream) != cudaSuccess) s = LBM_ERR_CUDA;
+            b->d_diag_flag = (int*)((char*)sc + 32);
+            if (cudaMemsetAsync(sc, 0, 64, b->stream) != cudaSuccess || write_step_slot(b) != cudaSuccess)
+                s = LBM_ERR_CUDA;
         }
     }
     if (s == LBM_OK) s = sync_descriptors(b);
@@ -852,8 +870,7 @@ lbm_status lbm_set_step(lbm_ctx* ctx, long long step)
         b->dirty = true;
     }
     b->host_step = step;
-    CK(cudaMemcpyAsync(b->d_step + (step & 1), &b->host_step, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
-    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    CK(write_step_slot(b));
     lbm_status s = refresh_alm(b);
     if (s != LBM_OK) return s;
     return check_device_errors(b);
@@ -948,8 +965,7 @@ lbm_status snapshot_restore(Batch* b, const Snapshot& S, long long step)
             ++k;
         }
     }
-    CK(cudaMemcpyAsync(b->d_step + cur, &b->host_step, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
-    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    CK(write_step_slot(b));
     return refresh_alm(b);
 }
 

@@ -85,6 +85,7 @@ struct StepArgs {
     int n_inst;
     int parity;                         // source array f[parity], destination f[parity ^ 1]
     long long* step_slot;               // step n in slot [parity]; CTA 0 writes n+1 to slot [parity ^ 1]
+    int* diag_flag;                     // slot [parity]: 1 if step n is a diagnostic step; CTA 0 writes n+1's
     unsigned int* diag_done;            // CTA completion counter, used on diagnostic steps only
     int diag_every;                     // diagnostic period shared by the batch (0 = off)
     int tile_z;                         // planes per CTA (1: no marching)

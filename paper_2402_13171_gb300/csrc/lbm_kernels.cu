@@ -22,7 +22,17 @@ namespace lbmgb {
 __host__ __device__ constexpr int qcx(int q) { return q % 3 - 1; }
 __host__ __device__ constexpr int qcy(int q) { return (q / 3) % 3 - 1; }
 __host__ __device__ constexpr int qcz(int q) { return q / 9 - 1; }
-__host__ __device__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+// One-axis weights 2/3 and 1/6 as FP32 values whose sum w1(-1) + w1(0) + w1(1)
+// is exactly 1 (2/3 rounded to nearest, 1/6 rounded down by 1e-8), so that the
+// equilibrium parts added by the collision carry no one-signed mass or
+// momentum error.
+__host__ __device__ constexpr float w1(int c) { return c == 0 ? 0x1.555556p-1f : 0x1.555554p-3f; }
+// w1(j) w1(k) for the x pass of the collision, rounded so that the nine values
+// also sum to exactly 1 (corner 1/36, edge 1/9, centre 4/9, each within 4e-8)
+__host__ __device__ constexpr float w2(int j, int k)
+{
+    return (j == 0 && k == 0) ? 0x1.c71c74p-2f : ((j == 0 || k == 0) ? 0x1.c71c7p-4f : 0x1.c71c7p-6f);
+}
 __host__ __device__ constexpr float wq(int q) { return w1(qcx(q)) * w1(qcy(q)) * w1(qcz(q)); }
 
 // ------------------------------------------------------------------ storage
@@ -139,29 +149,29 @@ __device__ __forceinline__ Moments raw_moments(const float h[27])
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         const float a = h[3 * r], b = h[3 * r + 1], c = h[3 * r + 2];
-        m0[r] = a + b + c;
-        m1[r] = c - a;
         m2[r] = c + a;
+        m0[r] = m2[r] + b;
+        m1[r] = c - a;
     }
     float A00[3], A10[3], A20[3], A01[3], A11[3], A02[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int r0 = 3 * k, r1 = 3 * k + 1, r2 = 3 * k + 2;
-        A00[k] = m0[r0] + m0[r1] + m0[r2];
+        A02[k] = m0[r2] + m0[r0];
+        A00[k] = A02[k] + m0[r1];
         A10[k] = m1[r0] + m1[r1] + m1[r2];
         A20[k] = m2[r0] + m2[r1] + m2[r2];
         A01[k] = m0[r2] - m0[r0];
         A11[k] = m1[r2] - m1[r0];
-        A02[k] = m0[r2] + m0[r0];
     }
     Moments M;
-    M.drho = A00[0] + A00[1] + A00[2];
+    M.Szz = A00[2] + A00[0];
+    M.drho = M.Szz + A00[1];
     M.jx = A10[0] + A10[1] + A10[2];
     M.jy = A01[0] + A01[1] + A01[2];
     M.jz = A00[2] - A00[0];
     M.Sxx = A20[0] + A20[1] + A20[2];
     M.Syy = A02[0] + A02[1] + A02[2];
-    M.Szz = A00[2] + A00[0];
     M.Sxy = A11[0] + A11[1] + A11[2];
     M.Sxz = A10[2] - A10[0];
     M.Syz = A01[2] - A01[0];
@@ -171,126 +181,166 @@ __device__ __forceinline__ Moments raw_moments(const float h[27])
 // ------------------------------------------------------------------ collisions
 
 // One-dimensional map from central moments (k0, k1, k2) about u to the three
-// populations at c = -1, 0, +1:
-//   f(0)  = (1 - u^2) k0 - 2u k1 - k2
-//   f(-1) = ((u^2 - u) k0 + (2u - 1) k1 + k2) / 2
-//   f(+1) = ((u^2 + u) k0 + (2u + 1) k1 + k2) / 2
-// with the u-dependent coefficients computed once per axis.
-struct Inv1d {
-    float a0, am, ap, bm, bp, m2u;
+// populations at c = -1, 0, +1, taking h2 = k2/2:
+//   f(-1) = dm k0 + (u - 1/2) k1 + h2,   f(+1) = dp k0 + (u + 1/2) k1 + h2,
+//   f(0)  = k0 - f(-1) - f(+1)           (the map preserves the zeroth moment)
+// with dm = (u^2 - u)/2 and dp = (u^2 + u)/2.  (dm, -u^2, dp) is also the
+// deviation dphi of the equilibrium factor phi(c) = w1(c) + dphi(c), the map
+// applied to the equilibrium central moments (1, 0, 1/3).
+struct Axis {
+    float dm, dp, u2, bm, bp;
 };
 
-__device__ __forceinline__ Inv1d inv1d_coeffs(float u)
+__device__ __forceinline__ Axis axis_of(float u)
 {
-    const float u2 = u * u;
-    Inv1d c;
-    c.a0 = 1.0f - u2;
-    c.am = 0.5f * (u2 - u);
-    c.ap = 0.5f * (u2 + u);
-    c.bm = u - 0.5f;
-    c.bp = u + 0.5f;
-    c.m2u = -2.0f * u;
-    return c;
+    Axis a;
+    a.u2 = u * u;
+    a.dm = 0.5f * (a.u2 - u);
+    a.dp = 0.5f * (a.u2 + u);
+    a.bm = u - 0.5f;
+    a.bp = u + 0.5f;
+    return a;
 }
 
-__device__ __forceinline__ void inv1d(const Inv1d& c, float k0, float k1, float k2, float& fm, float& f0, float& fp)
+__device__ __forceinline__ float dphi(const Axis& a, int c) { return c < 0 ? a.dm : (c > 0 ? a.dp : -a.u2); }
+
+// the map for general (k0, k1, h2) and for the zero patterns of the collided moments
+__device__ __forceinline__ void inv_full(const Axis& a, float k0, float k1, float h2, float& fm, float& f0, float& fp)
 {
-    const float h2 = 0.5f * k2;
-    fm = fmaf(c.am, k0, fmaf(c.bm, k1, h2));
-    fp = fmaf(c.ap, k0, fmaf(c.bp, k1, h2));
-    f0 = fmaf(c.a0, k0, fmaf(c.m2u, k1, -k2));
+    fm = fmaf(a.dm, k0, fmaf(a.bm, k1, h2));
+    fp = fmaf(a.dp, k0, fmaf(a.bp, k1, h2));
+    f0 = k0 - fm - fp;
+}
+__device__ __forceinline__ void inv_k1h2(const Axis& a, float k1, float h2, float& fm, float& f0, float& fp)
+{
+    fm = fmaf(a.bm, k1, h2);
+    fp = fmaf(a.bp, k1, h2);
+    f0 = -fm - fp;
+}
+__device__ __forceinline__ void inv_k0k1(const Axis& a, float k0, float k1, float& fm, float& f0, float& fp)
+{
+    fm = fmaf(a.dm, k0, a.bm * k1);
+    fp = fmaf(a.dp, k0, a.bp * k1);
+    f0 = k0 - fm - fp;
+}
+__device__ __forceinline__ void inv_k0h2(const Axis& a, float k0, float h2, float& fm, float& f0, float& fp)
+{
+    fm = fmaf(a.dm, k0, h2);
+    fp = fmaf(a.dp, k0, h2);
+    f0 = k0 - fm - fp;
+}
+__device__ __forceinline__ void inv_k1(const Axis& a, float k1, float& fm, float& f0, float& fp)
+{
+    fm = a.bm * k1;
+    fp = a.bp * k1;
+    f0 = -fm - fp;
 }
 
 // Cumulant collision with shear rate omega, bulk and all higher-order rates 1
 // (all cumulants above second order relax to zero, so post-collision central
 // moments of order 4 and 6 are the Gaussian products of the second-order ones,
 // orders 3 and 5 vanish), forcing by the velocity shift (first central moments
-// -F/2 -> +F/2).  Computed as h* = (feq(rho, u) - w) + L_u(Delta), Delta the
-// post-collision central moments minus those of the product equilibrium.
+// -F/2 -> +F/2).
+//
+// The post-collision central moments are K = rho e0 (x) e0 (x) e0 + Delta with
+// e0 = (1, 0, 1/3) the per-axis equilibrium moments and Delta the 16 nonzero
+// collided deviations.  The populations f* = L_x L_y L_z K are formed pass by
+// pass as offsets from the weights: since L_a e0 = w1 + dphi_a, each pass
+// carries only the deviation, adding the equilibrium part that it owns
+// (z: e0_a e0_b (dphi_z + drho phi_z), y: e0_a w1 dphi_y, x: w1 w1 dphi_x), so
+// no large term is ever subtracted (in the y and x passes the part enters the
+// pass input as the moments (0, u, -u^2), which the map takes to dphi).
+// Second-order indices are held halved
+// (moment (a, b, c) scaled by 2^-(number of indices equal to 2)), so that every
+// pass receives h2 = k2/2 directly.
 __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy, float Fz, float omega, float& drho_o,
                                                  float& jx_o, float& jy_o, float& jz_o)
 {
     const Moments M = raw_moments(h);
     const float rho = 1.0f + M.drho;
-    const float inv = 1.0f / rho;
-    const float ux = (M.jx + 0.5f * Fx) * inv;
-    const float uy = (M.jy + 0.5f * Fy) * inv;
-    const float uz = (M.jz + 0.5f * Fz) * inv;
+    // correctly rounded: the equilibrium momentum rho (j + F/2)/rho must not
+    // carry a one-signed reciprocal error, or the lattice momentum drifts
+    const float inv = __frcp_rn(rho);
+    const float hFx = 0.5f * Fx, hFy = 0.5f * Fy, hFz = 0.5f * Fz;
+    const float ux = (M.jx + hFx) * inv;
+    const float uy = (M.jy + hFy) * inv;
+    const float uz = (M.jz + hFz) * inv;
     const float third = 1.0f / 3.0f;
-    // second central moments minus rho/3 delta
-    const float axx = M.Sxx - M.drho * third - rho * ux * ux + ux * Fx;
-    const float ayy = M.Syy - M.drho * third - rho * uy * uy + uy * Fy;
-    const float azz = M.Szz - M.drho * third - rho * uz * uz + uz * Fz;
-    const float axy = M.Sxy - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
-    const float axz = M.Sxz - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
-    const float ayz = M.Syz - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
+    // second central moments minus rho/3 delta, using rho u = j + F/2:
+    //   S_ab - rho u_a u_b + (u_a F_b + u_b F_a)/2 = S_ab - j_a u_b + u_a F_b/2
+    const float t3 = M.drho * third;
+    const float axx = fmaf(ux, hFx - M.jx, M.Sxx - t3);
+    const float ayy = fmaf(uy, hFy - M.jy, M.Syy - t3);
+    const float azz = fmaf(uz, hFz - M.jz, M.Szz - t3);
+    const float axy = fmaf(-M.jx, uy, fmaf(ux, hFy, M.Sxy));
+    const float axz = fmaf(-M.jx, uz, fmaf(ux, hFz, M.Sxz));
+    const float ayz = fmaf(-M.jy, uz, fmaf(uy, hFz, M.Syz));
     const float om1 = 1.0f - omega;
     const float tr3 = (axx + ayy + azz) * third;
     const float bxx = om1 * (axx - tr3), byy = om1 * (ayy - tr3), bzz = om1 * (azz - tr3);
     const float bxy = om1 * axy, bxz = om1 * axz, byz = om1 * ayz;
-
-    float D[27];
-#pragma unroll
-    for (int m = 0; m < 27; ++m) D[m] = 0.0f;
-#define MI(a, b, c) ((c) * 9 + (b) * 3 + (a))
-    D[MI(1, 0, 0)] = 0.5f * Fx;
-    D[MI(0, 1, 0)] = 0.5f * Fy;
-    D[MI(0, 0, 1)] = 0.5f * Fz;
-    D[MI(2, 0, 0)] = bxx;
-    D[MI(0, 2, 0)] = byy;
-    D[MI(0, 0, 2)] = bzz;
-    D[MI(1, 1, 0)] = bxy;
-    D[MI(1, 0, 1)] = bxz;
-    D[MI(0, 1, 1)] = byz;
-    D[MI(2, 2, 0)] = (bxx + byy) * third + (bxx * byy + 2.0f * bxy * bxy) * inv;
-    D[MI(2, 0, 2)] = (bxx + bzz) * third + (bxx * bzz + 2.0f * bxz * bxz) * inv;
-    D[MI(0, 2, 2)] = (byy + bzz) * third + (byy * bzz + 2.0f * byz * byz) * inv;
-    D[MI(2, 1, 1)] = byz * third + (bxx * byz + 2.0f * bxy * bxz) * inv;
-    D[MI(1, 2, 1)] = bxz * third + (byy * bxz + 2.0f * bxy * byz) * inv;
-    D[MI(1, 1, 2)] = bxy * third + (bzz * bxy + 2.0f * bxz * byz) * inv;
+    const float inv2 = 0.5f * inv, inv4 = 0.25f * inv;
+    // collided deviations in the halved basis
+    const float d200 = 0.5f * bxx, d020 = 0.5f * byy, d002 = 0.5f * bzz;
+    const float d220 = (bxx + byy) * (1.0f / 12.0f) + (bxx * byy + 2.0f * bxy * bxy) * inv4;
+    const float d202 = (bxx + bzz) * (1.0f / 12.0f) + (bxx * bzz + 2.0f * bxz * bxz) * inv4;
+    const float d022 = (byy + bzz) * (1.0f / 12.0f) + (byy * bzz + 2.0f * byz * byz) * inv4;
+    const float d211 = byz * (1.0f / 6.0f) + (bxx * byz + 2.0f * bxy * bxz) * inv2;
+    const float d121 = bxz * (1.0f / 6.0f) + (byy * bxz + 2.0f * bxy * byz) * inv2;
+    const float d112 = bxy * (1.0f / 6.0f) + (bzz * bxy + 2.0f * bxz * byz) * inv2;
+    float d222;
     {
         const float sxx = bxx * inv, syy = byy * inv, szz = bzz * inv;
         const float sxy = bxy * inv, sxz = bxz * inv, syz = byz * inv;
         const float g = (sxx + syy + szz) * (1.0f / 9.0f) + (sxx * syy + sxx * szz + syy * szz) * third +
                         sxx * syy * szz + 2.0f * (third + sxx) * syz * syz + 2.0f * (third + syy) * sxz * sxz +
                         2.0f * (third + szz) * sxy * sxy + 8.0f * sxy * sxz * syz;
-        D[MI(2, 2, 2)] = rho * g;
+        d222 = (0.125f * rho) * g;
     }
-#undef MI
-    // inverse transform about u: z, then y, then x
-    const Inv1d cz = inv1d_coeffs(uz), cy = inv1d_coeffs(uy), cx = inv1d_coeffs(ux);
+    const Axis X = axis_of(ux), Y = axis_of(uy), Z = axis_of(uz);
+    // z pass over the columns (a, b); G[k][b][a], k the population index along z
+    float G[27];
+#define GZ(a, b) G[(b) * 3 + (a)], G[9 + (b) * 3 + (a)], G[18 + (b) * 3 + (a)]
+    inv_k1h2(Z, hFz, d002, GZ(0, 0));
+    inv_k0k1(Z, hFx, bxz, GZ(1, 0));
+    inv_k0h2(Z, d200, d202, GZ(2, 0));
+    inv_k0k1(Z, hFy, byz, GZ(0, 1));
+    inv_k0h2(Z, bxy, d112, GZ(1, 1));
+    inv_k1(Z, d211, GZ(2, 1));
+    inv_k0h2(Z, d020, d022, GZ(0, 2));
+    inv_k1(Z, d121, GZ(1, 2));
+    inv_k0h2(Z, d220, d222, GZ(2, 2));
+#undef GZ
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float fm, f0, fp;
-            inv1d(cz, D[b * 3 + a], D[9 + b * 3 + a], D[18 + b * 3 + a], fm, f0, fp);
-            D[b * 3 + a] = fm;
-            D[9 + b * 3 + a] = f0;
-            D[18 + b * 3 + a] = fp;
-        }
+    for (int k = 0; k < 3; ++k) {
+        const float dz = dphi(Z, k - 1);
+        const float gz = fmaf(M.drho, w1(k - 1) + dz, dz);  // rho phi_z - w1
+        G[k * 9 + 0] += gz;
+        G[k * 9 + 2] = fmaf(1.0f / 6.0f, gz, G[k * 9 + 2]);
+        G[k * 9 + 6] = fmaf(1.0f / 6.0f, gz, G[k * 9 + 6]);
+        G[k * 9 + 8] = fmaf(1.0f / 36.0f, gz, G[k * 9 + 8]);
+    }
+    // y pass over the columns (a, k); the equilibrium part e0_a w1 dphi_y enters
+    // as the moments (0, u_y, -u_y^2), which the map takes to dphi_y
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float fm, f0, fp;
-            inv1d(cy, D[k * 9 + a], D[k * 9 + 3 + a], D[k * 9 + 6 + a], fm, f0, fp);
-            D[k * 9 + a] = fm;
-            D[k * 9 + 3 + a] = f0;
-            D[k * 9 + 6 + a] = fp;
+            float k1 = G[k * 9 + 3 + a], h2 = G[k * 9 + 6 + a];
+            if (a != 1) {
+                const float e = (a == 0 ? 1.0f : 1.0f / 6.0f) * w1(k - 1);
+                k1 = fmaf(e, uy, k1);
+                h2 = fmaf(-0.5f * e, Y.u2, h2);
+            }
+            inv_full(Y, G[k * 9 + a], k1, h2, G[k * 9 + a], G[k * 9 + 3 + a], G[k * 9 + 6 + a]);
         }
+    // x pass over the rows (j, k), with w1 w1 dphi_x entered the same way
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
-        float fm, f0, fp;
-        inv1d(cx, D[3 * r], D[3 * r + 1], D[3 * r + 2], fm, f0, fp);
-        D[3 * r] = fm;
-        D[3 * r + 1] = f0;
-        D[3 * r + 2] = fp;
+        const float e = w2(r % 3 - 1, r / 3 - 1);
+        const float k1 = fmaf(e, ux, G[3 * r + 1]), h2 = fmaf(-0.5f * e, X.u2, G[3 * r + 2]);
+        inv_full(X, G[3 * r], k1, h2, h[3 * r], h[3 * r + 1], h[3 * r + 2]);
     }
-    float E[27];
-    feq_offsets(M.drho, ux, uy, uz, E);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) h[q] = E[q] + D[q];
     drho_o = M.drho;
     jx_o = M.jx + Fx;
     jy_o = M.jy + Fy;
@@ -764,13 +814,16 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
     const DevDomain* D = A.dom + inst;
     const long long step = __ldcg(A.step_slot + A.parity);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) A.step_slot[A.parity ^ 1] = step + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        A.step_slot[A.parity ^ 1] = step + 1;
+        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
     const int nx = D->nx, ny = D->ny, nz = D->nz;
     const int z1 = MARCH ? min(z0 + A.tile_z, nz) : z0 + 1;  // planes [z0, z1)
     const unsigned uN = (unsigned)D->N;
     const T* __restrict__ src = (const T*)D->f[A.parity];
     T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
-    const bool diag = A.diag_every > 0 && (step % A.diag_every) == 0;  // uniform over the grid
+    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;  // uniform over the grid
     float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
@@ -977,8 +1030,11 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
     const int tid = threadIdx.x;
     const int par = A.parity;
     const long long step = __ldcg(A.step_slot + par);
-    if (blockIdx.x == 0 && tid == 0) A.step_slot[par ^ 1] = step + 1;
-    const bool diag = A.diag_every > 0 && (step % A.diag_every) == 0;
+    if (blockIdx.x == 0 && tid == 0) {
+        A.step_slot[par ^ 1] = step + 1;
+        A.diag_flag[par ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
+    const bool diag = __ldcg(A.diag_flag + par) != 0;
     float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
 
     unsigned it = blockIdx.x;

@@ -267,10 +267,13 @@ class WindowMeans:
             self.ends.append(self.step)
 
 
-def converged_reference(wm, from_step):
-    """The converged mean (average of the window means after from_step) and its
-    noise floor (median relative L2 distance of those windows to it)."""
-    late = [m for m, e in zip(wm.means, wm.ends) if e > from_step]
+def converged_reference(wms, from_step):
+    """The converged mean (average of the window means after from_step, over
+    one run or several) and its noise floor (median relative L2 distance of
+    those windows to it)."""
+    if isinstance(wms, WindowMeans):
+        wms = [wms]
+    late = [m for wm in wms for m, e in zip(wm.means, wm.ends) if e > from_step]
     ref = np.mean(late, axis=0)
     noise = float(np.median([np.linalg.norm(m - ref) / np.linalg.norm(ref) for m in late]))
     return ref, noise

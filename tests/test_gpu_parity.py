@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 from paper_2402_13171_gb300 import inputs as I
-from cases import max_du, setup_pair
+from cases import gpu_lattice, max_du, setup_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -140,18 +140,28 @@ def test_rotor_short_horizon(coll):
 
 
 def test_rotor_force_sum_matches_blade_forces():
-    """One step of momentum change equals minus the applied blade forces."""
+    """One step of momentum change equals minus the applied blade forces.
+
+    The background is a uniform flow, whose cells all round alike in FP32; the
+    same lattice without the rotor is stepped beside it, so that every cell
+    outside the force support (bitwise the same in both) cancels and only the
+    spread force remains."""
     dom, turb = small_rotor_case()
     dom["bc"] = ("periodic", "periodic", "periodic")
-    g, s = setup_pair(dom, [turb], u=np.stack([np.full((40, 40, 64), 0.05), np.zeros((40, 40, 64)),
-                                               np.zeros((40, 40, 64))]))
+    u0 = np.stack([np.full((40, 40, 64), 0.05), np.zeros((40, 40, 64)), np.zeros((40, 40, 64))])
+    g, s = setup_pair(dom, [turb], u=u0)
+    g_free = gpu_lattice(dom)
+    g_free.init_fields(None, u0, None)
     C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
-    j0 = np.einsum("qa,qzyx->a", C, g.pdfs())
+    j0, j0_free = (np.einsum("qa,qzyx->a", C, L.pdfs()) for L in (g, g_free))
     _, _, ef0, _ = g.loads(0, elements=True)  # forces of step 0
     g.step(1)
-    j1 = np.einsum("qa,qzyx->a", C, g.pdfs())
-    # FP32 storage of ~1e5 cells rounds the summed momentum at the 1e-5 relative level
-    np.testing.assert_allclose(j1 - j0, -ef0.astype(np.float64).sum(0), rtol=2e-5, atol=1e-7)
+    g_free.step(1)
+    j1, j1_free = (np.einsum("qa,qzyx->a", C, L.pdfs()) for L in (g, g_free))
+    dj = (j1 - j0) - (j1_free - j0_free)
+    # ~2.5e4 cells in the force support, each rounding its momentum at ~1e-9
+    np.testing.assert_allclose(dj, -ef0.astype(np.float64).sum(0), rtol=2e-6, atol=1e-7)
+    g_free.destroy()
 
 
 def test_full_size_single_turbine_sampled():
