@@ -49,7 +49,7 @@ typedef enum {
     LBM_ERR_OOM = 2,         /* device allocation failed */
     LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     LBM_ERR_NUMERIC = 4,     /* NaN/Inf seen by the diagnostic sums */
-    LBM_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device wait (the staged step's copy barriers, ~1 s) gave up */
     LBM_ERR_STATE = 6,       /* call not valid in the current state */
     LBM_ERR_UNSUPPORTED = 7  /* combination not built */
 } lbm_status;
@@ -81,9 +81,10 @@ typedef struct {
     int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 32 x 4;
                                 tile_x a multiple of 32, tile_x * tile_y <= 256 */
     int tile_z;              /* planes per CTA, each thread marching through them; 0 = default 1; <= 64 */
-    int staged;              /* 1: stage the 27 source rows of each 1-row tile in shared memory with
-                                asynchronous copies, persistent CTAs (needs tile_y = tile_z = 1 and nx a
-                                multiple of 4 (FP32) or 8 (16-bit)); 0 = direct loads */
+    int staged;              /* 1: persistent CTAs stage the 27 source rows of each 1-row tile in a
+                                3-4 stage shared-memory ring filled by TMA bulk copies (needs
+                                tile_y = tile_z = 1 and nx a multiple of 4 (FP32) or 8 (16-bit));
+                                0 = direct loads */
 } lbm_config;
 
 typedef struct {

@@ -362,6 +362,7 @@ lbm_status check_device_errors(Batch* b)
         CK(cudaMemcpy(&e, I.h.err, sizeof e, cudaMemcpyDeviceToHost));
         if (e & ERR_NONFINITE) return fail(b, LBM_ERR_NUMERIC, "non-finite mass or momentum in the diagnostic sums");
         if (e & ERR_ELEMENT_OUTSIDE) return fail(b, LBM_ERR_STATE, "a blade element left the lattice interior");
+        if (e & ERR_TIMEOUT) return fail(b, LBM_ERR_TIMEOUT, "a bounded wait of the staged step gave up");
     }
     return LBM_OK;
 }

@@ -17,7 +17,7 @@ enum Coll : int { COLL_CUMULANT = 0, COLL_SRT_SMAG = 1 };
 enum Store : int { STORE_FP32 = 0, STORE_BF16 = 1, STORE_FP16 = 2 };
 
 // Device error bits (DevDomain::err).
-enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_ELEMENT_OUTSIDE = 2u };
+enum ErrBits : unsigned { ERR_NONFINITE = 1u, ERR_ELEMENT_OUTSIDE = 2u, ERR_TIMEOUT = 4u };
 
 // One rotor.  Rotor basis: e_axis = (cos yaw, sin yaw, 0), e1 = (-sin yaw,
 // cos yaw, 0), e2 = (0, 0, 1); blade direction e_r = cos(theta) e1 + sin(theta) e2.

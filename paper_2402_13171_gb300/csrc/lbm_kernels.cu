@@ -280,21 +280,27 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
     const float bxx = om1 * (axx - tr3), byy = om1 * (ayy - tr3), bzz = om1 * (azz - tr3);
     const float bxy = om1 * axy, bxz = om1 * axz, byz = om1 * ayz;
     const float inv2 = 0.5f * inv, inv4 = 0.25f * inv;
-    // collided deviations in the halved basis
+    const float b2xy = 2.0f * bxy, b2xz = 2.0f * bxz, b2yz = 2.0f * byz;
+    // collided deviations in the halved basis: orders 4 and 6 are the Gaussian
+    // (Isserlis) products of the collided second-order moments minus those of
+    // the equilibrium, expanded so that no equilibrium-sized term cancels
     const float d200 = 0.5f * bxx, d020 = 0.5f * byy, d002 = 0.5f * bzz;
-    const float d220 = (bxx + byy) * (1.0f / 12.0f) + (bxx * byy + 2.0f * bxy * bxy) * inv4;
-    const float d202 = (bxx + bzz) * (1.0f / 12.0f) + (bxx * bzz + 2.0f * bxz * bxz) * inv4;
-    const float d022 = (byy + bzz) * (1.0f / 12.0f) + (byy * bzz + 2.0f * byz * byz) * inv4;
-    const float d211 = byz * (1.0f / 6.0f) + (bxx * byz + 2.0f * bxy * bxz) * inv2;
-    const float d121 = bxz * (1.0f / 6.0f) + (byy * bxz + 2.0f * bxy * byz) * inv2;
-    const float d112 = bxy * (1.0f / 6.0f) + (bzz * bxy + 2.0f * bxz * byz) * inv2;
+    const float d220 = fmaf(bxx + byy, 1.0f / 12.0f, fmaf(bxx, byy, bxy * b2xy) * inv4);
+    const float d202 = fmaf(bxx + bzz, 1.0f / 12.0f, fmaf(bxx, bzz, bxz * b2xz) * inv4);
+    const float d022 = fmaf(byy + bzz, 1.0f / 12.0f, fmaf(byy, bzz, byz * b2yz) * inv4);
+    const float d211 = fmaf(byz, 1.0f / 6.0f, fmaf(bxx, byz, bxy * b2xz) * inv2);
+    const float d121 = fmaf(bxz, 1.0f / 6.0f, fmaf(byy, bxz, bxy * b2yz) * inv2);
+    const float d112 = fmaf(bxy, 1.0f / 6.0f, fmaf(bzz, bxy, bxz * b2yz) * inv2);
     float d222;
     {
+        // g = s_xx s_yy s_zz-type product of (1/3 + s) minus 1/27, plus the
+        // off-diagonal pairings, with s = b / rho
         const float sxx = bxx * inv, syy = byy * inv, szz = bzz * inv;
         const float sxy = bxy * inv, sxz = bxz * inv, syz = byz * inv;
-        const float g = (sxx + syy + szz) * (1.0f / 9.0f) + (sxx * syy + sxx * szz + syy * szz) * third +
-                        sxx * syy * szz + 2.0f * (third + sxx) * syz * syz + 2.0f * (third + syy) * sxz * sxz +
-                        2.0f * (third + szz) * sxy * sxy + 8.0f * sxy * sxz * syz;
+        const float p = sxx + syy, q = sxx * syy;
+        const float diag = fmaf(p + szz, 1.0f / 9.0f, fmaf(fmaf(szz, p, q), third, q * szz));
+        const float pair = fmaf(third + sxx, syz * syz, fmaf(third + syy, sxz * sxz, (third + szz) * (sxy * sxy)));
+        const float g = fmaf(2.0f, pair, fmaf(8.0f * sxy, sxz * syz, diag));
         d222 = (0.125f * rho) * g;
     }
     const Axis X = axis_of(ux), Y = axis_of(uy), Z = axis_of(uz);
@@ -962,71 +968,116 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
     }
 }
 
-// ------------------------------------------------------------------ staged step
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// ------------------------------------------------------------------ staged step (TMA bulk copies)
 
 // Elements per 16-byte chunk: the halo kept on each side of a staged row.
 template <typename T> __host__ __device__ constexpr int halo_of() { return 16 / (int)sizeof(T); }
 
-// Issue the asynchronous copies of one row segment (tile with tile_y = 1):
-// for each direction q, source row (y - c_y, z - c_z) (wrapped or clamped as
-// in load_cell), elements [x0 - H, x0 + W + H) clipped to the row, into
-// stage[q][x - x0 + H].  nx is a multiple of H, so every chunk is aligned.
-template <typename T>
-__device__ __forceinline__ void stage_issue(const DevDomain* D, const T* __restrict__ src, int x0, int y, int z, int W,
-                                            T* stage)
+// Stages of the shared-memory ring for a segment width: four while a stage
+// (27 rows of W + 2H elements) is at most 16 KB, else three.
+__host__ __device__ inline int bulk_stages(int width, int elem_bytes)
 {
-    constexpr int H = halo_of<T>();
-    const int nx = D->nx, ny = D->ny, nz = D->nz;
-    const int by = D->bc[1], bz = D->bc[2];
-    int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
-    if (by == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
-    else { ym = max(ym, 0); yp = min(yp, ny - 1); }
-    if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
-    else { zm = max(zm, 0); zp = min(zp, nz - 1); }
-    const int lo = max(x0 - H, 0), hi = min(x0 + W + H, nx);
-    const int nch = (hi - lo) / H;
-    const int rowlen = W + 2 * H;
-    const unsigned uN = (unsigned)D->N;
-    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    // one warp per direction q, one lane per 16-byte chunk of its row
-    for (int q = threadIdx.x >> 5; q < 27; q += nwarps) {
-        const int j = (q / 3) % 3, kk = q / 9;
-        const int ys = j == 0 ? yp : (j == 1 ? y : ym);
-        const int zs = kk == 0 ? zp : (kk == 1 ? z : zm);
-        const T* row = src + ((unsigned)q * uN + ((unsigned)zs * (unsigned)ny + (unsigned)ys) * (unsigned)nx);
-        T* dst = stage + q * rowlen + (lo - x0 + H);
-        for (int c = lane; c < nch; c += 32) cp_async16(dst + c * H, row + lo + c * H);
-    }
-    cp_async_commit();
+    const int stage = 27 * (width + 2 * (16 / elem_bytes)) * elem_bytes;
+    return stage <= 16384 ? 4 : 3;
+}
+__host__ __device__ inline size_t bulk_smem_bytes(int width, int elem_bytes)
+{
+    return (size_t)bulk_stages(width, elem_bytes) * 27 * (width + 2 * (16 / elem_bytes)) * elem_bytes;
 }
 
-// k_step with the source rows staged in shared memory: persistent CTAs walk
-// the work list (one row segment of blockDim.x cells per entry) and copy the
-// next segment's 27 rows asynchronously while the current one collides, so
-// the loads in flight cost no registers.  Same arithmetic, same results as
-// k_step.
+constexpr int kMaxStages = 4;
+constexpr long long kWaitCycles = 1ll << 31;  // ~1 s of SM clock before a wait is declared failed
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase of the given parity; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_addr(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+// One row of bytes (16-byte aligned, multiple of 16) from global to shared memory,
+// completing on the barrier's transaction count.
+__device__ __forceinline__ void bulk_row(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Issue the 27 row copies of work-list entry `it` (a row segment, tile_y = 1)
+// into `stage`: lane q copies direction q's source row (y - c_y, z - c_z),
+// wrapped or clamped as in load_cell, elements [x0 - H, x0 + W + H) clipped to
+// the row, to stage[q][x - x0 + H].  nx is a multiple of H, so the copy starts
+// and ends on 16-byte boundaries.  Warp-wide; lane 0 arms the barrier.
+template <typename T>
+__device__ __forceinline__ void bulk_issue(const StepArgs& A, unsigned it, T* stage, unsigned long long* bar, int W)
+{
+    constexpr int H = halo_of<T>();
+    const int lane = threadIdx.x & 31;
+    const unsigned long long tile = A.tiles[it];
+    const DevDomain* D = A.dom + ((tile >> 48) & 0x7FFF);
+    const int z = (int)((tile >> 32) & 0xFFFF), y = (int)((tile >> 16) & 0xFFFF), x0 = (int)(tile & 0xFFFF);
+    const int nx = D->nx, ny = D->ny, nz = D->nz;
+    const int lo = max(x0 - H, 0), hi = min(x0 + W + H, nx);
+    const unsigned bytes = (unsigned)(hi - lo) * (unsigned)sizeof(T);
+    if (lane == 0) mbar_expect_tx(bar, 27u * bytes);
+    __syncwarp();
+    if (lane < 27) {
+        const int q = lane;
+        int ys = y - ((q / 3) % 3 - 1), zs = z - (q / 9 - 1);
+        const int by = D->bc[1], bz = D->bc[2];
+        if (ys < 0) ys = by == BC_PERIODIC ? ys + ny : 0;
+        if (ys >= ny) ys = by == BC_PERIODIC ? ys - ny : ny - 1;
+        if (zs < 0) zs = bz == BC_PERIODIC ? zs + nz : 0;
+        if (zs >= nz) zs = bz == BC_PERIODIC ? zs - nz : nz - 1;
+        const T* row = (const T*)D->f[A.parity] + ((unsigned)q * (unsigned)D->N + ((unsigned)zs * ny + ys) * (unsigned)nx);
+        bulk_row(stage + q * (W + 2 * H) + (lo - x0 + H), row + lo, bytes, bar);
+    }
+}
+
+// k_step with the source rows staged in shared memory by TMA bulk copies:
+// persistent CTAs walk the work list (one row segment of blockDim.x cells per
+// entry) through a ring of 3-4 stages, so two or three segments are in flight
+// while one collides and the loads in flight hold no registers.  Same
+// arithmetic, same results as k_step.  Every barrier wait is bounded: a wait
+// that gives up sets ERR_TIMEOUT, and the CTA waits (bounded) for its copies in
+// flight before it returns.
 template <int COLL, typename T>
 __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
 {
     constexpr int H = halo_of<T>();
     constexpr int kCull = 128;
-    extern __shared__ __align__(16) unsigned char stage_raw[];
+    extern __shared__ __align__(128) unsigned char stage_raw[];
+    __shared__ __align__(8) unsigned long long s_full[kMaxStages];
     __shared__ double s_red[8][4];
-    __shared__ int s_flag;
+    __shared__ int s_flag, s_abort;
     __shared__ float4 s_pos[kCull], s_frc[kCull];
     __shared__ int s_tag[kCull];
     __shared__ int s_cnt[8];
     const int W = blockDim.x;
     const int rowlen = W + 2 * H;
-    T* stages[2] = {(T*)stage_raw, (T*)stage_raw + 27 * rowlen};
+    const int S = bulk_stages(W, (int)sizeof(T));
+    T* const stage0 = (T*)stage_raw;
     const int tid = threadIdx.x;
     const int par = A.parity;
     const long long step = __ldcg(A.step_slot + par);
@@ -1036,15 +1087,46 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
     }
     const bool diag = __ldcg(A.diag_flag + par) != 0;
     float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    const unsigned G = gridDim.x;
+    // segments of this CTA: blockIdx.x + k G, k = 0, 1, ...
+    const unsigned n_mine = blockIdx.x < A.n_tiles ? (A.n_tiles - blockIdx.x + G - 1) / G : 0u;
 
-    unsigned it = blockIdx.x;
-    if (it < A.n_tiles) {
-        const unsigned long long t0 = A.tiles[it];
-        const DevDomain* D0 = A.dom + ((t0 >> 48) & 0x7FFF);
-        stage_issue<T>(D0, (const T*)D0->f[par], (int)(t0 & 0xFFFF), (int)((t0 >> 16) & 0xFFFF),
-                       (int)((t0 >> 32) & 0xFFFF), W, stages[0]);
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) mbar_init(s_full + i, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = 0; it < A.n_tiles; ++k, it += gridDim.x) {
+    __syncthreads();
+    // prologue: the first S - 1 segments
+    if (tid < 32)
+        for (unsigned k = 0; k < (unsigned)(S - 1) && k < n_mine; ++k)
+            bulk_issue<T>(A, blockIdx.x + k * G, stage0 + (size_t)k * 27 * rowlen, s_full + k, W);
+    unsigned issued = min((unsigned)(S - 1), n_mine);
+    unsigned k = 0;  // segments waited for
+
+    for (; k < n_mine; ++k) {
+        const unsigned it = blockIdx.x + k * G;
+        // every thread is done with segment k - 1, whose stage the next copy reuses
+        __syncthreads();
+        if (s_abort) break;
+        if (issued < n_mine) {
+            if (tid < 32) {
+                if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                bulk_issue<T>(A, blockIdx.x + issued * G, stage0 + (size_t)(issued % S) * 27 * rowlen,
+                              s_full + issued % S, W);
+            }
+            ++issued;
+        }
+        const int sidx = (int)(k % S);
+        if (!mbar_wait(s_full + sidx, (k / S) & 1u)) {
+            s_abort = 1;
+            atomicOr(A.dom->err, ERR_TIMEOUT);
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const T* st = stage0 + (size_t)sidx * 27 * rowlen;
+
         const unsigned long long tile = A.tiles[it];
         const bool rotor_tile = (tile >> 63) != 0;
         const DevDomain* D = A.dom + ((tile >> 48) & 0x7FFF);
@@ -1056,17 +1138,6 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
         const unsigned uN = (unsigned)D->N;
         const T* __restrict__ src = (const T*)D->f[par];
         T* __restrict__ dst = (T*)D->f[par ^ 1];
-        const T* st = stages[k & 1];
-        cp_async_wait_all();
-        __syncthreads();
-        // next segment's rows go to the other buffer (read in the previous iteration)
-        const unsigned nit = it + gridDim.x;
-        if (nit < A.n_tiles) {
-            const unsigned long long tn = A.tiles[nit];
-            const DevDomain* Dn = A.dom + ((tn >> 48) & 0x7FFF);
-            stage_issue<T>(Dn, (const T*)Dn->f[par], (int)(tn & 0xFFFF), (int)((tn >> 16) & 0xFFFF),
-                           (int)((tn >> 32) & 0xFFFF), W, stages[(k + 1) & 1]);
-        }
         // rotor segment: cull the blade elements reaching it
         int n_cull = -1;
         if (rotor_tile) {
@@ -1211,7 +1282,6 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
                     for (int w = 0; w < (W >> 5); ++w) sum += s_red[w][kk];
                     atomicAdd(D->diag_acc + kk, sum);
                 }
-            __syncthreads();
         }
         // last rotor segment of this lattice: actuator line of the next step
         if (rotor_tile) {
@@ -1229,7 +1299,14 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
             }
         }
     }
-    cp_async_wait_all();
+    // after a failed wait: the copies still in flight (segments k .. issued - 1)
+    // land before the CTA exits, each wait bounded again
+    if (s_abort) {
+        __syncthreads();
+        if (tid == 0)
+            for (unsigned j = k; j < issued; ++j) (void)mbar_wait(s_full + j % S, (j / S) & 1u);
+        __syncthreads();
+    }
     // diagnostic step: the last CTA closes the sums of every lattice
     if (diag && tid == 0) {
         __threadfence();
@@ -1385,7 +1462,7 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
 #define LBM_STEP_CASE(C, S, T)                                                                        \
     if (coll == C && store == S) {                                                                    \
         if (a.staged) {                                                                               \
-            const size_t smem = 2 * 27 * (size_t)(block.x + 2 * halo_of<T>()) * sizeof(T);            \
+            const size_t smem = bulk_smem_bytes((int)block.x, (int)sizeof(T));                        \
             k_step_staged<C, T><<<grid, block, smem, s>>>(a);                                         \
         } else if (march) {                                                                           \
             k_step<C, T, true><<<grid, block, 0, s>>>(a);                                             \
@@ -1411,7 +1488,7 @@ int staged_blocks_per_sm(int coll, int store, int width)
     int n = 0;
 #define LBM_OCC_CASE(C, S, T)                                                                                    \
     if (coll == C && store == S) {                                                                               \
-        const size_t smem = 2 * 27 * (size_t)(width + 2 * halo_of<T>()) * sizeof(T);                            \
+        const size_t smem = bulk_smem_bytes(width, (int)sizeof(T));                                              \
         if (cudaFuncSetAttribute(k_step_staged<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != \
             cudaSuccess)                                                                                         \
             return 0;                                                                                            \
