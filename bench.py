@@ -56,6 +56,22 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_max(values, dist=None, device="cpu"):
+    """The maximum over ranks of each value (every rank receives it): the job's
+    time is the slowest rank's."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_mlups(world, cells, steps, elapsed_ms):
+    """Whole-job throughput of `world` replicas, each advancing `cells` cells by
+    `steps` steps, in the slowest rank's time."""
+    return world * cells * steps / (elapsed_ms * 1e-3) / 1e6
+
+
 # DRAM bytes per k_step launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of `bench.py --tile <tile> --steps 20 --warmup 3`, keyed
 # by (workload, storage, collision, tile).  They hold for the kernel source
@@ -287,11 +303,8 @@ def run_ours(args):
     elapsed_ms = e0.elapsed_time(e1)
     kernel_ms, launches = lat.kernel_time()
     lat.set_profiling(False)
-    t_local = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    elapsed_ms, kernel_ms = float(t_local[0]), float(t_local[1])
-    value = world * cells * args.steps / (elapsed_ms * 1e-3) / 1e6
+    elapsed_ms, kernel_ms = reduce_max([elapsed_ms, kernel_ms], dist, device="cuda")
+    value = job_mlups(world, cells, args.steps, elapsed_ms)
     peak, peak_kind = load_peaks()
     achieved = bytes_per_cell * cells / (kernel_ms * 1e-3) / 1e9
     thrust, torque = lat.loads(0)
@@ -313,11 +326,8 @@ def run_ours(args):
         rho_o, u_o = lat.moments()
         barrier()
         dt = time.perf_counter() - t
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt[0])
-        e2e = {"value": world * cells * args.steps / dt / 1e6, "unit": "MLUPS",
+        dt = reduce_max([dt], dist, device="cuda")[0]
+        e2e = {"value": job_mlups(world, cells, args.steps, dt * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": 16.0 * N / args.steps,
                "d2h_bytes_per_step": 16.0 + 32.0 * N / args.steps,
                "api": "lbm_init_fields(host rho, u) + K x (lbm_step(1) + alm_get_loads) + lbm_get_moments"}
