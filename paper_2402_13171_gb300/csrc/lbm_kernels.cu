@@ -686,6 +686,17 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
 
 // ------------------------------------------------------------------ the time step
 
+// A work-list entry, read with an L2 evict-last policy: the list is read once per
+// step among the PDF streams, and without the hint it would be evicted and
+// cost every CTA a DRAM round trip before its first PDF load.
+__device__ __forceinline__ unsigned long long ld_tile(const unsigned long long* p)
+{
+    unsigned long long v, pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Pulled pre-collision populations of cell (x, y, z): clamped/wrapped loads,
 // then the inlet and wall rules.
 template <typename T>
@@ -812,7 +823,7 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
     __shared__ float4 s_pos[kCull], s_frc[kCull];
     __shared__ int s_tag[kCull];
     __shared__ int s_cnt[8];
-    const unsigned long long tile = A.tiles[blockIdx.x];
+    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
     const bool rotor_tile = (tile >> 63) != 0;
     const int inst = (int)((tile >> 48) & 0x7FFF);
     const int z0 = (int)((tile >> 32) & 0xFFFF);
