@@ -100,6 +100,28 @@ def measured_traffic(workload, storage, collision, tile):
     return NCU_TRAFFIC["bytes"].get((workload, storage, collision, tile))
 
 
+def bytes_per_cell_update(q=27, force_components=0, elem_bytes=4):
+    """Algorithmic bytes of one cell update: q loads and q stores of the
+    storage type, plus a dense force field if one is read (Sec. 4.3 counts 3
+    components; the fused gather here reads none)."""
+    return (2 * q + force_components) * elem_bytes
+
+
+def max_mlups(bandwidth_gbs, bytes_per_cell):
+    """Bandwidth-bound ceiling of the update rate, P_max = b_S / n_b (Sec. 4.3)."""
+    return bandwidth_gbs * 1e9 / bytes_per_cell / 1e6
+
+
+def lightspeed(bandwidth_gbs, flops_per_cell, peak_gflops, bytes_per_cell):
+    """l = min(1, B_m / B_c) with machine balance b_S / P_peak and code balance
+    n_b / n_f (Sec. 4.3): below 1 the kernel is bandwidth-bound."""
+    return min(1.0, bandwidth_gbs * flops_per_cell / (peak_gflops * bytes_per_cell))
+
+
+def achieved_gbs(bytes_per_cell, cells, seconds):
+    return bytes_per_cell * cells / seconds / 1e9
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -306,7 +328,7 @@ def run_ours(args):
     elapsed_ms, kernel_ms = reduce_max([elapsed_ms, kernel_ms], dist, device="cuda")
     value = job_mlups(world, cells, args.steps, elapsed_ms)
     peak, peak_kind = load_peaks()
-    achieved = bytes_per_cell * cells / (kernel_ms * 1e-3) / 1e9
+    achieved = achieved_gbs(bytes_per_cell, cells, kernel_ms * 1e-3)
     thrust, torque = lat.loads(0)
     diag_sums, diag_step = lat.diagnostics()
 
