@@ -43,10 +43,11 @@ def parse_args():
     p.add_argument("--tile", type=str, default="auto",
                    help="CTA tile XxY, XxYxZ or XxYxZxS (S = 1: rows staged in shared memory), or 'auto' "
                         "(the library's autotuner, cached)")
-    p.add_argument("--workload", choices=["single", "batch16", "precision", "warmstart"], default="single",
+    p.add_argument("--workload", choices=["single", "batch16", "precision", "warmstart", "tilesweep"], default="single",
                    help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices in one launch per "
                         "step; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles; "
-                        "warmstart: 3x3 farm, steps to a settled mean from a cold vs a surrogate warm start")
+                        "warmstart: 3x3 farm, steps to a settled mean from a cold vs a surrogate warm start; "
+                        "tilesweep: the single-rotor workload at every tile candidate of the tuner")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -562,6 +563,54 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+# The tuner's candidates (tile_x, tile_y, tile_z, load mode), as in lbm_autotune.
+TILE_CANDIDATES = [(32, 4, 1, 0), (32, 2, 1, 0), (32, 8, 1, 0), (64, 2, 1, 0), (64, 1, 1, 0), (128, 1, 1, 0),
+                   (32, 4, 2, 0), (32, 4, 4, 0), (32, 2, 4, 0), (32, 2, 8, 0), (64, 2, 4, 0), (32, 4, 8, 0),
+                   (64, 1, 1, 1), (128, 1, 1, 1), (256, 1, 1, 1)]
+
+
+def run_tilesweep(args):
+    """The single-rotor workload at every tile candidate of the tuner: the
+    k_step time per launch (CUDA events over --steps launches after --warmup)
+    and its fraction of the HBM roofline.  Under `ncu --metrics
+    dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_step` it gives the
+    DRAM bytes of every tile in one pass."""
+    import torch
+
+    from paper_2402_13171_gb300 import build as B
+    from paper_2402_13171_gb300 import inputs as I
+    from paper_2402_13171_gb300 import lbm
+
+    B.build()
+    torch.cuda.set_device(0)
+    peak, peak_kind = load_peaks()
+    rows = []
+    for tile in TILE_CANDIDATES:
+        dom, turb = I.single_turbine_case()
+        lat = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], nu=dom["nu"], storage=args.storage, bc=dom["bc"],
+                                 seed=dom["seed"], tile=tile, diag_every=DIAG_EVERY)
+        lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
+        lat.add_turbine(**turb)
+        lat.step(args.warmup)
+        lat.sync()
+        lat.set_profiling(True)
+        lat.step(args.steps)
+        lat.sync()
+        ms, _ = lat.kernel_time()
+        bpc, cells = lat.traffic_model()
+        rows.append({"tile": "x".join(str(v) for v in tile[:3]) + (" staged" if tile[3] else ""),
+                     "kernel_ms": ms, "mlups": cells / ms / 1e3,
+                     "frac": achieved_gbs(bpc, cells, ms * 1e-3) / peak})
+        lat.destroy()
+    best = max(rows, key=lambda r: r["mlups"])
+    line = {"metric": METRIC, "value": best["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD + "_tilesweep", "storage": args.storage,
+                                            "peak_gbs": peak, "peak_kind": peak_kind},
+            "tiles": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -570,6 +619,8 @@ def main():
         run_precision(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "tilesweep":
+        run_tilesweep(args)
     else:
         run_ours(args)
 

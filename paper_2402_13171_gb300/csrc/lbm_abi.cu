@@ -279,6 +279,7 @@ lbm_status sync_descriptors(Batch* b)
     tiles.insert(tiles.end(), rest.begin(), rest.end());
     if (tiles.size() > b->tiles_cap) {
         if (b->d_tiles) dfree(b, b->d_tiles);
+        b->tiles_cap = 0;
         b->d_tiles = (unsigned long long*)dalloc(b, sizeof(unsigned long long) * tiles.size());
         if (!b->d_tiles) return fail(b, LBM_ERR_OOM, "work list allocation failed");
         b->tiles_cap = tiles.size();
@@ -736,9 +737,16 @@ lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, d
     if (n > b->probe_cap) {
         dfree(b, b->d_probe);
         dfree(b, b->d_probe_out);
+        b->probe_cap = 0;
         b->d_probe = (long long*)dalloc(b, sizeof(long long) * n);
         b->d_probe_out = (double*)dalloc(b, sizeof(double) * 4 * n);
-        if (!b->d_probe || !b->d_probe_out) return fail(b, LBM_ERR_OOM, "probe buffer allocation failed");
+        if (!b->d_probe || !b->d_probe_out) {
+            dfree(b, b->d_probe);
+            dfree(b, b->d_probe_out);
+            b->d_probe = nullptr;
+            b->d_probe_out = nullptr;
+            return fail(b, LBM_ERR_OOM, "probe buffer allocation failed");
+        }
         b->probe_cap = n;
     }
     CK(cudaMemcpyAsync(b->d_probe, cells, sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));

@@ -286,6 +286,7 @@ lbm_status ensure_batch(mlp_ctx* c, int B)
     free_dev(c, c->T);
     free_dev(c, c->dY);
     free_dev(c, c->sq);
+    c->cap = 0;  // set again only once every buffer is in place
     c->A.assign(L + 1, nullptr);
     c->Z.assign(L + 1, nullptr);
     c->A[0] = malloc_dev<float>(c, (size_t)B * c->n_in);
@@ -495,6 +496,7 @@ lbm_status mlp_set_data(mlp_ctx* c, const float* x, const float* target, int n)
     if (!c || !x || !target || n < 1) return LBM_ERR_INVALID_ARG;
     free_dev(c, c->data_x);
     free_dev(c, c->data_t);
+    c->n_data = 0;  // set again only once the data is on the device
     c->data_x = malloc_dev<float>(c, (size_t)n * c->n_in);
     c->data_t = malloc_dev<float>(c, (size_t)n * c->n_out);
     if (!c->data_x || !c->data_t) return mlp_fail(c, LBM_ERR_OOM, "dataset allocation failed");
