@@ -74,15 +74,44 @@ def job_mlups(world, cells, steps, elapsed_ms):
 
 
 # DRAM bytes per k_step launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of `bench.py --tile <tile> --steps 20 --warmup 3`, keyed
-# by (workload, storage, collision, tile).  They hold for the kernel source
-# whose SHA-256 is recorded and are reported as null once it changes.
+# of the single-rotor workload at every tile candidate, from one ncu pass over
+# `bench.py --workload tilesweep --steps 1 --warmup 1 --storage <fp32|bf16>`
+# (the second, warm launch of each tile), keyed by (workload, storage,
+# collision, tile).  They hold for the kernel source whose SHA-256 is recorded
+# and are reported as null once it changes.
 NCU_TRAFFIC = {
     "kernel_sha256": "debd8a08068644c06ead8572ef9cd205c268198ed22491637203d0c54ff9efea",
     "bytes": {
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x1"): 464803072 + 410214400,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x8"): 464869888 + 406981632,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x1"): 243484160 + 191635200,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x1"): 464497408 + 406221056,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x1"): 464896768 + 406456576,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x8x1"): 464242944 + 408297216,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x1"): 459270912 + 406795264,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1"): 459541760 + 408531456,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1"): 459192832 + 405345536,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x2"): 464589568 + 404506624,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x4"): 464569088 + 402696704,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x4"): 464660480 + 403674368,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x8"): 464733952 + 406027008,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x4"): 459424512 + 403784192,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x8"): 464661248 + 403681280,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1 staged"): 584604160 + 410151168,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1 staged"): 478787584 + 400759296,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "256x1x1 staged"): 454902016 + 401781760,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x1"): 243056640 + 185731328,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x1"): 243340544 + 186890496,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x8x1"): 242799616 + 189598208,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x1"): 232526080 + 183576320,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1"): 232924928 + 185371904,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1"): 232450560 + 183852800,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x2"): 243286272 + 186260992,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x4"): 243256320 + 185110784,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x4"): 243409152 + 183821824,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x8"): 242799360 + 186279936,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x4"): 232773120 + 182963200,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x8"): 242708224 + 184458496,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1 staged"): 257354240 + 183936768,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1 staged"): 243033600 + 181532160,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "256x1x1 staged"): 227327488 + 181519360,
     },
 }
 
