@@ -422,6 +422,7 @@ def run_ours(args):
             "accuracy": {"max_du_vs_fp64_oracle": acc, "case": "48x32x32 rotor, 50 steps"} if acc is not None else None,
             "loads": {"thrust": thrust, "torque": torque},
             "diagnostics": {"step": diag_step, "sum_drho": diag_sums[0], "momentum": list(diag_sums[1:])},
+            "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
     for L in lattices:
@@ -591,6 +592,16 @@ def run_warmstart(args):
     net.destroy()
     print(json.dumps(line), flush=True)
 
+
+# The paper's own single-device figures (Sec. 4, table of estimated and measured
+# kernel performance; FP32, 64 cells per rotor diameter, NewMexico rotor):
+# context from other hardware, not a target.
+PAPER_CONTEXT = {
+    "NVIDIA A100-SXM-80GB": {"mlups_with_turbine": 1677.0, "mlups_without": 1866.5, "stream_copy_gbs": 1713.0,
+                             "fraction_of_bandwidth_bound": 0.223, "bytes_per_cell": 228},
+    "AMD EPYC 7763 (64 cores)": {"mlups_with_turbine": 202.1, "mlups_without": 204.0, "stream_copy_gbs": 105.2,
+                                 "fraction_of_bandwidth_bound": 0.438, "bytes_per_cell": 228},
+}
 
 # The tuner's candidates (tile_x, tile_y, tile_z, load mode), as in lbm_autotune.
 TILE_CANDIDATES = [(32, 4, 1, 0), (32, 2, 1, 0), (32, 8, 1, 0), (64, 2, 1, 0), (64, 1, 1, 0), (128, 1, 1, 0),

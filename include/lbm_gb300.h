@@ -146,8 +146,9 @@ lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, con
  * element counts (at most 4096 elements per lattice). */
 lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* desc, int* id_out);
 
-/* Enqueue n_steps time steps on the stream (replays of a captured CUDA graph
- * when profiling is off).  Errors from earlier steps surface here or at the
+/* Enqueue n_steps time steps on the stream: replays of captured 8- and 2-step
+ * CUDA graphs (a single launch for an odd last step; plain launches on the
+ * legacy default stream).  Errors from earlier steps surface here or at the
  * next synchronising call. */
 lbm_status lbm_step(lbm_ctx* ctx, int n_steps);
 
@@ -204,9 +205,11 @@ lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z, int
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[4],
                         double* best_ms);
 
-/* Kernel timing: when enabled, lbm_step launches kernels one by one with CUDA
- * events around every stream-collide launch; lbm_get_kernel_time returns the
- * mean duration (ms) and the number of timed launches since enabling. */
+/* Kernel timing: when enabled, lbm_step brackets every replay of its 8- or
+ * 2-step graph (or a single step launch) with CUDA events on the lattice's stream, so
+ * timing does not break up the replays; lbm_get_kernel_time returns the mean
+ * duration per step launch (ms) and the number of timed launches since
+ * enabling. */
 lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable);
 lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches);
 

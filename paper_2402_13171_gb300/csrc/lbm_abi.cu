@@ -56,11 +56,12 @@ struct Batch {
     std::string err;
     bool dirty = true;
     bool profiling = false;
-    std::vector<cudaEvent_t> ev;
+    std::vector<cudaEvent_t> ev;         // pairs bracketing timed launches
+    std::vector<int> ev_launches;        // step launches inside each pair
     size_t ev_used = 0;
     double prof_ms = 0.0;
     long long prof_n = 0;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [long?][start parity]
     long long* d_probe = nullptr;   // probe cell list and results, grown on demand
     double* d_probe_out = nullptr;
     int probe_cap = 0;
@@ -118,11 +119,12 @@ void dfree(Batch* b, void* p)
 
 void drop_graphs(Batch* b)
 {
-    for (auto& g : b->gexec)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (auto& row : b->gexec)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
 }
 
 void destroy_batch(Batch* b)
@@ -637,6 +639,42 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     return LBM_OK;
 }
 
+// Add the recorded event pairs to the running kernel time and free the pool.
+lbm_status fold_events(Batch* b)
+{
+    if (b->ev_used == 0) return LBM_OK;
+    CK(cudaEventSynchronize(b->ev[b->ev_used - 1]));
+    for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
+        b->prof_ms += ms;
+        b->prof_n += b->ev_launches[i / 2];
+    }
+    b->ev_used = 0;
+    return LBM_OK;
+}
+
+// Steps per replay of the short and the long captured graph.
+constexpr int kGraphSteps[2] = {2, 8};
+
+// The captured graph of kGraphSteps[len] steps starting at parity p (source
+// array f[p]); an even number of steps ends on the same parity.
+lbm_status ensure_graph(Batch* b, int len, int p)
+{
+    if (b->gexec[len][p]) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status s = LBM_OK;
+    for (int i = 0; i < kGraphSteps[len] && s == LBM_OK; ++i) s = launch_one(b, p ^ (i & 1));
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (s != LBM_OK) return b->status;
+    CK(e);
+    e = cudaGraphInstantiate(&b->gexec[len][p], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
 {
     ENTER(ctx);
@@ -645,7 +683,9 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
     if (s != LBM_OK) return s;
     int left = n_steps;
     if (b->profiling) {
-        for (; left > 0; --left) {
+        // events bracket each graph replay (two steps) or single launch, so
+        // timing does not break up the replays
+        while (left > 0) {
             if (b->ev_used + 2 > b->ev.size()) {
                 if (b->ev.size() < 32768) {
                     cudaEvent_t e0, e1;
@@ -653,45 +693,43 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
                     CK(cudaEventCreate(&e1));
                     b->ev.push_back(e0);
                     b->ev.push_back(e1);
+                    b->ev_launches.push_back(0);
                 } else {
-                    // fold the recorded pairs into the running sum and reuse the pool
-                    CK(cudaEventSynchronize(b->ev[b->ev_used - 1]));
-                    for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
-                        float ms = 0.f;
-                        CK(cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
-                        b->prof_ms += ms;
-                        b->prof_n++;
-                    }
-                    b->ev_used = 0;
+                    s = fold_events(b);
+                    if (s != LBM_OK) return s;
                 }
             }
+            const int p = (int)(b->host_step & 1);
+            const int len = left >= kGraphSteps[1] ? 1 : 0;
+            const int k = (b->stream && left >= 2) ? kGraphSteps[len] : 1;
+            if (k > 1) {
+                s = ensure_graph(b, len, p);
+                if (s != LBM_OK) return s;
+            }
             CK(cudaEventRecord(b->ev[b->ev_used], b->stream));
-            s = launch_one(b, (int)(b->host_step & 1));
-            if (s != LBM_OK) return s;
+            if (k > 1) {
+                CK(cudaGraphLaunch(b->gexec[len][p], b->stream));
+            } else {
+                s = launch_one(b, p);
+                if (s != LBM_OK) return s;
+            }
             CK(cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
+            b->ev_launches[b->ev_used / 2] = k;
             b->ev_used += 2;
-            b->host_step++;
+            b->host_step += k;
+            left -= k;
         }
         return LBM_OK;
     }
-    if (b->stream && left >= 2) {
+    for (int len = 1; b->stream && len >= 0; --len) {
         const int p = (int)(b->host_step & 1);
-        if (!b->gexec[p]) {
-            cudaGraph_t g = nullptr;
-            CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            lbm_status s1 = launch_one(b, p);
-            lbm_status s2 = s1 == LBM_OK ? launch_one(b, p ^ 1) : s1;
-            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-            if (s1 != LBM_OK || s2 != LBM_OK) return b->status;
-            CK(e);
-            e = cudaGraphInstantiate(&b->gexec[p], g, 0);
-            cudaGraphDestroy(g);
-            CK(e);
-        }
-        while (left >= 2) {
-            CK(cudaGraphLaunch(b->gexec[p], b->stream));
-            left -= 2;
-            b->host_step += 2;
+        if (left < kGraphSteps[len]) continue;
+        s = ensure_graph(b, len, p);
+        if (s != LBM_OK) return s;
+        while (left >= kGraphSteps[len]) {
+            CK(cudaGraphLaunch(b->gexec[len][p], b->stream));
+            left -= kGraphSteps[len];
+            b->host_step += kGraphSteps[len];
         }
     }
     for (; left > 0; --left) {
@@ -1095,16 +1133,8 @@ lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable)
 lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches)
 {
     ENTER(ctx);
-    if (b->ev_used > 0) {
-        CK(cudaEventSynchronize(b->ev[b->ev_used - 1]));
-        for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
-            b->prof_ms += ms;
-            b->prof_n++;
-        }
-        b->ev_used = 0;
-    }
+    lbm_status s = fold_events(b);
+    if (s != LBM_OK) return s;
     if (mean_ms) *mean_ms = b->prof_n ? b->prof_ms / (double)b->prof_n : 0.0;
     if (launches) *launches = b->prof_n;
     return LBM_OK;
