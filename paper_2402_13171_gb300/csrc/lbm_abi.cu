@@ -62,6 +62,7 @@ struct Batch {
     double prof_ms = 0.0;
     long long prof_n = 0;
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [long?][start parity]
+    unsigned n_rotor = 0;                 // rotor tiles at the head of the work list
     long long* d_probe = nullptr;   // probe cell list and results, grown on demand
     double* d_probe_out = nullptr;
     int probe_cap = 0;
@@ -287,6 +288,7 @@ lbm_status sync_descriptors(Batch* b)
         b->tiles_cap = tiles.size();
     }
     b->n_tiles = (unsigned)tiles.size();
+    b->n_rotor = (unsigned)rotor.size();
     CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(unsigned long long) * tiles.size(), cudaMemcpyHostToDevice,
                        b->stream));
     std::vector<DevDomain> doms;
@@ -304,6 +306,8 @@ StepArgs step_args(Batch* b, int parity)
     a.dom = b->d_dom;
     a.tiles = b->d_tiles;
     a.n_tiles = b->n_tiles;
+    a.n_total = b->n_tiles;
+    a.write_step = 1;
     a.n_inst = (int)b->inst.size();
     a.parity = parity;
     a.step_slot = b->d_step;
@@ -328,10 +332,27 @@ cudaError_t write_step_slot(Batch* b)
     return e;
 }
 
+// One time step.  Staged rows: one persistent launch over the whole work list.
+// Otherwise two launches of k_step: the rotor tiles (first in the list), then
+// the rest, allowed to overlap the rotor launch; the step counter is advanced
+// by the second (or by the only one).
 lbm_status launch_one(Batch* b, int parity)
 {
-    const dim3 grid(b->staged ? std::min(b->n_tiles, b->staged_grid) : b->n_tiles), block(b->tile_x, b->tile_y);
-    CK(launch_step(b->coll, b->store, grid, block, b->stream, step_args(b, parity)));
+    const StepArgs a = step_args(b, parity);
+    const dim3 block(b->tile_x, b->tile_y);
+    if (b->staged) {
+        CK(launch_step(b->coll, b->store, dim3(std::min(b->n_tiles, b->staged_grid)), block, b->stream, a, false,
+                       false));
+        return LBM_OK;
+    }
+    const unsigned R = b->n_rotor, Nb = b->n_tiles - b->n_rotor;
+    StepArgs ar = a, ab = a;
+    ar.n_tiles = R;
+    ar.write_step = Nb == 0 ? 1 : 0;
+    ab.tiles = b->d_tiles + R;
+    ab.n_tiles = Nb;
+    if (R > 0) CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));
+    if (Nb > 0) CK(launch_step(b->coll, b->store, dim3(Nb), block, b->stream, ab, false, R > 0));
     return LBM_OK;
 }
 

@@ -80,8 +80,10 @@ struct DevDomain {
 // Arguments of one stream-collide launch over all lattices of a batch.
 struct StepArgs {
     const DevDomain* dom;               // device array
-    const unsigned long long* tiles;    // work list
-    unsigned int n_tiles;
+    const unsigned long long* tiles;    // this launch's part of the work list (the rotor tiles, or the rest)
+    unsigned int n_tiles;               // entries in that part
+    unsigned int n_total;               // entries of the whole step (both launches): diagnostic close-out
+    int write_step;                     // 1 for the one launch per step whose CTA 0 advances the step slot
     int n_inst;
     int parity;                         // source array f[parity], destination f[parity ^ 1]
     long long* step_slot;               // step n in slot [parity]; CTA 0 writes n+1 to slot [parity ^ 1]
@@ -101,7 +103,12 @@ __host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0,
 }
 
 // Host-side launchers (lbm_kernels.cu).
-cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a);
+// rotor: the launch over the rotor tiles (element culling, force gather, the
+// actuator line of the next step) rather than over the rest.  dependent: a
+// bulk launch that directly follows its own step's rotor launch on the stream
+// and may overlap it (programmatic stream serialization).
+cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
+                        bool dependent);
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
 int staged_blocks_per_sm(int coll, int store, int width);
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);

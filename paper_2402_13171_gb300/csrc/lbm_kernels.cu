@@ -811,44 +811,31 @@ __device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, 
     }
 }
 
-// One time step over the work list.  A CTA covers tile_x x tile_y cells of
-// tile_z consecutive planes; with MARCH a thread walks its column of planes and
-// issues the loads of the next plane before the collision of the current one.
-template <int COLL, typename T, bool MARCH>
-__global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
+// The update of one rotor tile: cull the blade elements whose support reaches
+// the tile into shared memory (in element order; when more than KCULL reach it
+// every cell scans all elements), then each cell as in the bulk path plus the
+// Gaussian-regularised blade force, and in the last rotor tile of its lattice
+// to finish, the actuator line of the next step.  CTA-wide; only the rotor
+// launch of k_step contains it.  Adds the cells' diagnostic partial sums to
+// sums[4].
+template <int COLL, typename T, bool MARCH, int KCULL>
+__device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned long long tile, long long step, int parity,
+                                               int tile_z, float4* s_pos, float4* s_frc, int* s_tag, int* s_cnt,
+                                               int* s_flag, float* sums)
 {
-    constexpr int kCull = 128;  // blade elements kept per rotor tile
-    __shared__ double s_red[8][4];
-    __shared__ int s_flag;
-    __shared__ float4 s_pos[kCull], s_frc[kCull];
-    __shared__ int s_tag[kCull];
-    __shared__ int s_cnt[8];
-    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
-    const bool rotor_tile = (tile >> 63) != 0;
-    const int inst = (int)((tile >> 48) & 0x7FFF);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
     const int z0 = (int)((tile >> 32) & 0xFFFF);
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
-    const DevDomain* D = A.dom + inst;
-    const long long step = __ldcg(A.step_slot + A.parity);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-        A.step_slot[A.parity ^ 1] = step + 1;
-        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
-    }
     const int nx = D->nx, ny = D->ny, nz = D->nz;
-    const int z1 = MARCH ? min(z0 + A.tile_z, nz) : z0 + 1;  // planes [z0, z1)
+    const int z1 = MARCH ? min(z0 + tile_z, nz) : z0 + 1;  // planes [z0, z1)
     const unsigned uN = (unsigned)D->N;
-    const T* __restrict__ src = (const T*)D->f[A.parity];
-    T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
-    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;  // uniform over the grid
-    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthreads = blockDim.x * blockDim.y;
+    const T* __restrict__ src = (const T*)D->f[parity];
+    T* __restrict__ dst = (T*)D->f[parity ^ 1];
 
-    // rotor tile: keep the blade elements whose support reaches the tile, in
-    // element order (n_cull = -1: too many, every cell scans all elements)
-    int n_cull = -1;
-    if (rotor_tile) {
+    int n_cull;
+    {
         const float tx0 = (float)(tile & 0xFFFF), ty0 = (float)((tile >> 16) & 0xFFFF);
         const float tx1 = tx0 + (float)(blockDim.x - 1), ty1 = ty0 + (float)(blockDim.y - 1);
         const float tz0 = (float)z0, tz1 = (float)(z1 - 1);
@@ -877,7 +864,7 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
                 chunk += s_cnt[w];
             }
             const int pos = off + __popc(m & ((1u << lane) - 1u));
-            if (keep && pos < kCull) {
+            if (keep && pos < KCULL) {
                 s_pos[pos] = pe;
                 s_frc[pos] = __ldg(Fe + e);
                 s_tag[pos] = t;
@@ -885,9 +872,10 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
             total += chunk;
             __syncthreads();
         }
-        n_cull = total <= kCull ? total : -1;
+        n_cull = total <= KCULL ? total : -1;
     }
 
+    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
     if (x < nx && y < ny) {
         float hn[27];
         load_cell<T>(D, src, x, y, z0, step, hn);
@@ -897,7 +885,6 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
 #pragma unroll
             for (int q = 0; q < 27; ++q) h[q] = hn[q];
             if (MARCH && z + 1 < z1) load_cell<T>(D, src, x, y, z + 1, step, hn);
-            // the x = 0 lane of each row prepares the inlet velocity of its column for step n+1
             if (D->bc[0] == BC_INOUT && x == 0) {
                 float u[3];
                 inflow_velocity(D, step + 1, y, z, u);
@@ -907,9 +894,8 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
                 ub[plane + col] = u[1];
                 ub[2 * plane + col] = u[2];
             }
-            // force: body + regularised blade forces inside the rotor boxes
             float F[3] = {D->body[0], D->body[1], D->body[2]};
-            if (rotor_tile) rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
+            rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
             float m, jx, jy, jz;
             if (COLL == COLL_CUMULANT)
                 collide_cumulant(h, F[0], F[1], F[2], D->omega, m, jx, jy, jz);
@@ -924,20 +910,108 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
             for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
         }
     }
+    sums[0] += o_m;
+    sums[1] += o_jx;
+    sums[2] += o_jy;
+    sums[3] += o_jz;
 
-    // last rotor CTA of this lattice: actuator line of the next step
-    if (rotor_tile) {
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(D->rotor_counter, 1u);
-            s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_flag) {
-            __threadfence();
-            alm_compute<T>(D, dst, step + 1);
-            if (tid == 0) *D->rotor_counter = 0u;
+    // last rotor tile of this lattice: actuator line of the next step
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(D->rotor_counter, 1u);
+        *s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*s_flag) {
+        __threadfence();
+        alm_compute<T>(D, dst, step + 1);
+        if (tid == 0) *D->rotor_counter = 0u;
+    }
+}
+
+// One time step over the work list, as two launches of this kernel: ROTOR over
+// the rotor tiles, then the rest (almost all of the lattice), whose code then
+// carries none of the rotor path.  A CTA covers tile_x x tile_y cells of tile_z
+// consecutive planes; with MARCH a thread walks its column of planes and issues
+// the loads of the next plane before the collision of the current one.
+// The rotor CTAs allow the dependent (bulk) launch to start as soon as they are
+// all running, so the two overlap and the actuator line of the next step,
+// evaluated by the last rotor CTA, runs under the bulk.  The two launches
+// write disjoint cells.  The bulk launch's last CTA waits for the rotor launch
+// before it exits, so the bulk launch ends only after both.
+template <int COLL, typename T, bool MARCH, bool ROTOR>
+__global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
+{
+    if (ROTOR) asm volatile("griddepcontrol.launch_dependents;");
+    constexpr int kCull = 128;  // blade elements kept per rotor tile
+    __shared__ double s_red[8][4];
+    __shared__ int s_flag;
+    __shared__ float4 s_pos[kCull], s_frc[kCull];
+    __shared__ int s_tag[kCull];
+    __shared__ int s_cnt[8];
+    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
+    const int inst = (int)((tile >> 48) & 0x7FFF);
+    const int z0 = (int)((tile >> 32) & 0xFFFF);
+    const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
+    const int x = (int)(tile & 0xFFFF) + threadIdx.x;
+    const DevDomain* D = A.dom + inst;
+    const long long step = __ldcg(A.step_slot + A.parity);
+    if (A.write_step && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        A.step_slot[A.parity ^ 1] = step + 1;
+        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
+    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;  // uniform over the grid
+    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+
+    if constexpr (ROTOR) {
+        float sums[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        rotor_tile_update<COLL, T, MARCH, kCull>(D, tile, step, A.parity, A.tile_z, s_pos, s_frc, s_tag, s_cnt,
+                                                 &s_flag, sums);
+        o_m = sums[0];
+        o_jx = sums[1];
+        o_jy = sums[2];
+        o_jz = sums[3];
+    } else {
+        const int nx = D->nx, ny = D->ny, nz = D->nz;
+        if (x < nx && y < ny) {
+            const int z1 = MARCH ? min(z0 + A.tile_z, nz) : z0 + 1;  // planes [z0, z1)
+            const unsigned uN = (unsigned)D->N;
+            const T* __restrict__ src = (const T*)D->f[A.parity];
+            T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
+            float hn[27];
+            load_cell<T>(D, src, x, y, z0, step, hn);
+#pragma unroll 1
+            for (int z = z0; z < z1; ++z) {
+                float h[27];
+#pragma unroll
+                for (int q = 0; q < 27; ++q) h[q] = hn[q];
+                if (MARCH && z + 1 < z1) load_cell<T>(D, src, x, y, z + 1, step, hn);
+                // the x = 0 lane of each row prepares the inlet velocity of its column for step n+1
+                if (D->bc[0] == BC_INOUT && x == 0) {
+                    float u[3];
+                    inflow_velocity(D, step + 1, y, z, u);
+                    float* ub = D->inflow_u[(step + 1) & 1];
+                    const int plane = ny * nz, col = z * ny + y;
+                    ub[col] = u[0];
+                    ub[plane + col] = u[1];
+                    ub[2 * plane + col] = u[2];
+                }
+                float m, jx, jy, jz;
+                if (COLL == COLL_CUMULANT)
+                    collide_cumulant(h, D->body[0], D->body[1], D->body[2], D->omega, m, jx, jy, jz);
+                else
+                    collide_srt_smag(h, D->body[0], D->body[1], D->body[2], D->tau0, D->smag_c2, m, jx, jy, jz);
+                o_m += m;
+                o_jx += jx;
+                o_jy += jy;
+                o_jz += jz;
+                const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+#pragma unroll
+                for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
+            }
         }
     }
     // diagnostic step (uniform over the grid): FP64 sums, closed by the last CTA
@@ -959,7 +1033,7 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
             }
             __threadfence();
             const unsigned prev = atomicAdd(A.diag_done, 1u);
-            if (prev == A.n_tiles - 1u) {
+            if (prev == A.n_total - 1u) {
                 __threadfence();
                 for (int i = 0; i < A.n_inst; ++i) {
                     const DevDomain* Di = A.dom + i;
@@ -976,6 +1050,9 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
                 *A.diag_done = 0u;
             }
         }
+    }
+    if constexpr (!ROTOR) {
+        if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     }
 }
 
@@ -1467,7 +1544,27 @@ static int grid_for(long long n, int block)
     return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
 }
 
-cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a)
+// A launch that may start while the kernel before it on the stream still runs
+// (programmatic stream serialization): as soon as every CTA of that kernel has
+// signalled griddepcontrol.launch_dependents.
+static cudaError_t launch_dependent(void (*kernel)(StepArgs), dim3 grid, dim3 block, cudaStream_t s,
+                                    const StepArgs& a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
+                        bool dependent)
 {
     const bool march = a.tile_z > 1;
 #define LBM_STEP_CASE(C, S, T)                                                                        \
@@ -1476,9 +1573,13 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
             const size_t smem = bulk_smem_bytes((int)block.x, (int)sizeof(T));                        \
             k_step_staged<C, T><<<grid, block, smem, s>>>(a);                                         \
         } else if (march) {                                                                           \
-            k_step<C, T, true><<<grid, block, 0, s>>>(a);                                             \
+            if (rotor) k_step<C, T, true, true><<<grid, block, 0, s>>>(a);                            \
+            else if (dependent) return launch_dependent(k_step<C, T, true, false>, grid, block, s, a);  \
+            else k_step<C, T, true, false><<<grid, block, 0, s>>>(a);                                 \
         } else {                                                                                      \
-            k_step<C, T, false><<<grid, block, 0, s>>>(a);                                            \
+            if (rotor) k_step<C, T, false, true><<<grid, block, 0, s>>>(a);                           \
+            else if (dependent) return launch_dependent(k_step<C, T, false, false>, grid, block, s, a); \
+            else k_step<C, T, false, false><<<grid, block, 0, s>>>(a);                                \
         }                                                                                             \
         return cudaGetLastError();                                                                    \
     }
