@@ -73,45 +73,46 @@ def job_mlups(world, cells, steps, elapsed_ms):
     return world * cells * steps / (elapsed_ms * 1e-3) / 1e6
 
 
-# DRAM bytes per k_step launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# of the single-rotor workload at every tile candidate, from one ncu pass over
+# DRAM bytes per time step (dram__bytes_read.sum + dram__bytes_write.sum over
+# the step's k_step launches: the rotor tiles and the rest) of the single-rotor
+# workload at every tile candidate, from one ncu pass over
 # `bench.py --workload tilesweep --steps 1 --warmup 1 --storage <fp32|bf16>`
-# (the second, warm launch of each tile), keyed by (workload, storage,
-# collision, tile).  They hold for the kernel source whose SHA-256 is recorded
-# and are reported as null once it changes.
+# (the second, warm step of each tile), keyed by (workload, storage, collision,
+# tile).  They hold for the kernel source whose SHA-256 is recorded and are
+# reported as null once it changes.
 NCU_TRAFFIC = {
-    "kernel_sha256": "debd8a08068644c06ead8572ef9cd205c268198ed22491637203d0c54ff9efea",
+    "kernel_sha256": "7b9eaa4c69411242ec5b7ef02c62e67d40bc1ef023a96203eec86fda6167e133",
     "bytes": {
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x1"): 464497408 + 406221056,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x1"): 464896768 + 406456576,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x8x1"): 464242944 + 408297216,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x1"): 459270912 + 406795264,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1"): 459541760 + 408531456,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1"): 459192832 + 405345536,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x2"): 464589568 + 404506624,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x4"): 464569088 + 402696704,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x4"): 464660480 + 403674368,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x8"): 464733952 + 406027008,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x4"): 459424512 + 403784192,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x8"): 464661248 + 403681280,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1 staged"): 584604160 + 410151168,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1 staged"): 478787584 + 400759296,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "256x1x1 staged"): 454902016 + 401781760,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x1"): 243056640 + 185731328,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x1"): 243340544 + 186890496,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x8x1"): 242799616 + 189598208,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x1"): 232526080 + 183576320,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1"): 232924928 + 185371904,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1"): 232450560 + 183852800,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x2"): 243286272 + 186260992,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x4"): 243256320 + 185110784,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x4"): 243409152 + 183821824,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x8"): 242799360 + 186279936,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x4"): 232773120 + 182963200,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x8"): 242708224 + 184458496,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1 staged"): 257354240 + 183936768,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1 staged"): 243033600 + 181532160,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "256x1x1 staged"): 227327488 + 181519360,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x1"): 464006400 + 387715584,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x1"): 464268800 + 387752192,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x8x1"): 463886848 + 390479360,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x1"): 458843136 + 373369856,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1"): 459151616 + 375493632,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1"): 458738688 + 372319744,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x2"): 464124416 + 387775488,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x4"): 464050176 + 386168576,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x4"): 464122112 + 386985216,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x8"): 464239360 + 389414400,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x4"): 458777344 + 371334912,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x8"): 464339456 + 387495168,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1 staged"): 580595456 + 409993728,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1 staged"): 478353408 + 400805888,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "256x1x1 staged"): 454901248 + 402104576,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x1"): 242792960 + 176521728,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x1"): 243091456 + 177986816,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x8x1"): 242638848 + 180159744,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x1"): 232361984 + 166520064,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1"): 232535552 + 168115200,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1"): 232282368 + 166939648,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x2"): 242996224 + 177754112,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x4"): 242923520 + 176738560,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x4"): 242983424 + 175547904,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x8"): 242989824 + 177702912,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x4"): 232286208 + 166548480,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x8"): 242866432 + 175930880,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1 staged"): 256952064 + 183855360,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1 staged"): 243158016 + 181501184,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "256x1x1 staged"): 227342080 + 181572608,
     },
 }
 
