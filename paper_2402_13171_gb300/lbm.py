@@ -350,21 +350,21 @@ class Lattice:
             pass
 
 
-def batch_create(configs, device=0):
-    """configs: list of dicts of make_config keyword arguments (nx, ny, nz, ...).
+def batch_create(cfgs, device=0):
+    """cfgs: list of dicts of make_config keyword arguments (nx, ny, nz, ...).
     Returns one Lattice per instance; stepping any steps all."""
     L = load()
     stream, alloc = Lattice._stream_and_alloc(device)
-    arr = (LbmConfig * len(configs))()
-    for i, kw in enumerate(configs):
+    arr = (LbmConfig * len(cfgs))()
+    for i, kw in enumerate(cfgs):
         kw = dict(kw)
         nx, ny, nz = kw.pop("nx"), kw.pop("ny"), kw.pop("nz")
         arr[i] = make_config(nx, ny, nz, stream_ptr=stream.cuda_stream, allocator=alloc, **kw)
-    hs = (ctypes.c_void_p * len(configs))()
-    _check_status(L.lbm_batch_create(len(configs), arr, hs), None, "lbm_batch_create")
+    hs = (ctypes.c_void_p * len(cfgs))()
+    _check_status(L.lbm_batch_create(len(cfgs), arr, hs), None, "lbm_batch_create")
     keep = {"stream": stream, "alloc": alloc, "cfg": arr}
-    return [Lattice(hs[i], (configs[i]["nx"], configs[i]["ny"], configs[i]["nz"]), keep,
-                    configs[i].get("storage", "fp32")) for i in range(len(configs))]
+    return [Lattice(hs[i], (cfgs[i]["nx"], cfgs[i]["ny"], cfgs[i]["nz"]), keep,
+                    cfgs[i].get("storage", "fp32")) for i in range(len(cfgs))]
 
 
 def _check_status(s, handle, what):

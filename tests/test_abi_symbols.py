@@ -14,7 +14,7 @@ def libpath():
     return B.build()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = lbm.header_functions()
     for n in ("lbm_create", "lbm_set_inflow", "alm_add_turbine", "lbm_step", "lbm_get_moments", "lbm_destroy"):
         assert n in names

@@ -247,7 +247,7 @@ def test_staged_batch_matches_direct():
         np.testing.assert_allclose(da, db, rtol=0, atol=1e-9)
 
 
-def test_autotune_keeps_state_and_results():
+def test_autotune_keeps_state_and_results(tmp_path):
     """The tuner times tile candidates on the live state and restores it: the
     run continues exactly as an untuned one."""
     import os
@@ -256,7 +256,7 @@ def test_autotune_keeps_state_and_results():
     gb, _ = setup_pair(dom, [turb], inflow=True)
     ga.step(5)
     gb.step(5)
-    cache = os.path.join(os.path.dirname(__file__), "..", "gpurun_out", "tune_cache_test.txt")
+    cache = str(tmp_path / "tune_cache.txt")
     if os.path.exists(cache):
         os.remove(cache)
     tile, ms = gb.autotune(steps=3, cache=cache)

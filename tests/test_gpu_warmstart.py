@@ -1,7 +1,7 @@
 """What the trained wake surrogate gains: a two-rotor tandem farm started from
 the surrogate's superposed wakes reaches the converged mean hub-plane velocity
 in fewer steps than the same farm started from the uniform inflow.  The plain
-solver stays the judge: the converged mean is the second half of a long cold
+solver decides: the converged mean is the second half of a long cold
 run, and a run counts as settled at the first 1000-step window whose mean is
 within twice that run's noise floor of it.
 
