@@ -11,9 +11,11 @@
  *   5. pull streaming with boundary rules, and
  *   6. cumulant collision (Geier et al. 2015, Sec. 2.1) or BGK-Smagorinsky with Guo forcing
  *      (Sec. 2.1, lattice Boltzmann equation with source term).
- * Steps 5-6 run fused in one kernel over the lattice; steps 1-4 of step n+1
- * run inside the kernel of step n as soon as the cells around the rotor are
- * written, so a time step is a single kernel launch.
+ * Steps 5-6 run fused in one kernel over the lattice, launched twice per time
+ * step: over the tiles around the rotors, then over the rest, the second
+ * overlapping the first.  Steps 1-4 of step n+1 run inside the rotor launch of
+ * step n as soon as the cells around the rotor are written, under the bulk
+ * launch, so the actuator line adds no serial gap.
  *
  * Conventions shared by every call:
  *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, relaxation rate omega = 1/(3 nu + 1/2).
@@ -123,8 +125,8 @@ typedef struct {
  * Errors: INVALID_ARG (sizes, collision/storage/bc codes, nu <= 0), OOM, CUDA. */
 lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out);
 
-/* Create n lattices that step together in one launch per time step (the
- * batched form of lbm_step).  cfgs[i] may differ in sizes, viscosity, inflow
+/* Create n lattices that step together: the same two launches per time step
+ * cover all of them (the batched form of lbm_step).  cfgs[i] may differ in sizes, viscosity, inflow
  * and rotors, but collision, storage and cuda_stream must agree
  * (UNSUPPORTED otherwise).  out receives n handles; lbm_step on any of them
  * advances all n.  Each handle is destroyed with lbm_destroy; memory is freed
@@ -147,8 +149,8 @@ lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, con
 lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* desc, int* id_out);
 
 /* Enqueue n_steps time steps on the stream: replays of captured 8- and 2-step
- * CUDA graphs (a single launch for an odd last step; plain launches on the
- * legacy default stream).  Errors from earlier steps surface here or at the
+ * CUDA graphs (plain launches for an odd last step and on the legacy default
+ * stream).  Errors from earlier steps surface here or at the
  * next synchronising call. */
 lbm_status lbm_step(lbm_ctx* ctx, int n_steps);
 
@@ -213,8 +215,8 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
 lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable);
 lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches);
 
-/* Algorithmic bytes one stream-collide launch moves per cell (27 loads + 27
- * stores of the storage type) and the number of cells of one launch. */
+/* Algorithmic bytes one time step moves per cell (27 loads + 27 stores of
+ * the storage type) and the number of cells of one step (all lattices). */
 lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_launch);
 
 /* Actuator-line evaluation for callers that cannot allocate device memory:

@@ -704,8 +704,8 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
     if (s != LBM_OK) return s;
     int left = n_steps;
     if (b->profiling) {
-        // events bracket each graph replay (two steps) or single launch, so
-        // timing does not break up the replays
+        // events bracket each graph replay (eight or two steps) or a single
+        // step, so timing does not break up the replays
         while (left > 0) {
             if (b->ev_used + 2 > b->ev.size()) {
                 if (b->ev.size() < 32768) {

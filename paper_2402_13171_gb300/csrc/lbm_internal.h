@@ -83,7 +83,7 @@ struct StepArgs {
     const unsigned long long* tiles;    // this launch's part of the work list (the rotor tiles, or the rest)
     unsigned int n_tiles;               // entries in that part
     unsigned int n_total;               // entries of the whole step (both launches): diagnostic close-out
-    int write_step;                     // 1 for the one launch per step whose CTA 0 advances the step slot
+    int write_step;                     // 1 for the launch of a step whose CTA 0 advances the step slot
     int n_inst;
     int parity;                         // source array f[parity], destination f[parity ^ 1]
     long long* step_slot;               // step n in slot [parity]; CTA 0 writes n+1 to slot [parity ^ 1]

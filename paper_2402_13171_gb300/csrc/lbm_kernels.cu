@@ -1,15 +1,15 @@
 // sm_103a kernels of the D3Q27 LBM + actuator line time step (arxiv 2402.13171).
 //
-// k_step: one fused pass per time step over every cell of every lattice of a
+// k_step: the fused pass of a time step over every cell of every lattice of a
 // batch: pull streaming with boundary rules (Sec. 2.1, streaming step), force
 // (body force + Gaussian-regularised blade forces, Sec. 2.2, gathered in the
 // rotor box), collision (cumulant, Sec. 2.1 / Geier et al. 2015, or BGK with a
 // Smagorinsky eddy viscosity), store.  PDFs live in HBM as offsets h = f - w
-// in the storage type; all arithmetic is FP32.  The CTAs covering the rotor
-// boxes are first in the work list; the last of them to finish evaluates the
-// actuator line for the next step (blade kinematics of Algorithm 2, trilinear
-// sampling, blade-element forces, FP64 rotor loads) while the remaining CTAs
-// stream the bulk of the lattice, so a time step is a single launch.
+// in the storage type; all arithmetic is FP32.  A step is two launches: the
+// tiles covering the rotor boxes, then the rest, which overlaps the first.  The
+// last rotor tile to finish evaluates the actuator line for the next step
+// (blade kinematics of Algorithm 2, trilinear sampling, blade-element forces,
+// FP64 rotor loads) while the bulk of the lattice streams.
 #include "lbm_internal.h"
 
 #include <cuda_bf16.h>
