@@ -16,6 +16,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                                                     inlet/outlet constant-state invariance
   blade kinematics, sampling, element forces ...... frozen-field closed form, affine exactness
   Gaussian spreading .............................. force-sum, separable closed form
+  Roma discrete-delta spreading ................... Roma's three moment conditions, force-sum,
+                                                    force centroid at the element
 """
 from __future__ import annotations
 
@@ -94,6 +96,7 @@ class Turbine(ctypes.Structure):
         ("twist", _dp),
         ("n_polar", ctypes.c_int),
         ("alpha", _dp), ("cl", _dp), ("cd", _dp),
+        ("kernel", ctypes.c_int),
     ]
 
 
@@ -125,8 +128,11 @@ def _declare(L):
     L.or_alm_forces.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), _dp, _dp, c_long, _dp, _dp, _dp, _dp]
     L.or_gauss_axis_sum.argtypes = [ctypes.c_double, ctypes.c_double]
     L.or_gauss_axis_sum.restype = ctypes.c_double
-    L.or_spread.argtypes = [ctypes.POINTER(Domain), _dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
-    L.or_spread_at.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    L.or_spread.argtypes = [ctypes.POINTER(Domain), _dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
+    L.or_spread_at.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, _dp]
+    L.or_roma_phi.argtypes = [ctypes.c_double]
+    L.or_roma_phi.restype = ctypes.c_double
     L.or_step.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), ctypes.c_int, _dp, _dp, _dp, _dp, c_long,
                           _dp, _dp, _dp]
     L.or_step_planes.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), ctypes.c_int, _dp, _dp, _dp, _dp,
@@ -226,6 +232,14 @@ def gauss_axis_sum(p, eps):
     return lib().or_gauss_axis_sum(float(p), float(eps))
 
 
+KERNEL = {"gauss": 0, "roma": 1}
+
+
+def roma_phi(r):
+    """Roma et al.'s three-point discrete delta at r (Sec. 2.2)."""
+    return lib().or_roma_phi(float(r))
+
+
 # ---------------------------------------------------------------- domain
 
 BC = {"periodic": 0, "inout": 1, "noslip": 2, "freeslip": 3}
@@ -256,7 +270,7 @@ class TurbineSpec:
     """Owns the numpy arrays an oracle Turbine struct points into."""
 
     def __init__(self, hub, radius, n_blades, n_elements, epsilon, omega, alpha, cl, cd, yaw=0.0, pitch=0.0,
-                 theta0=0.0, chord_root=1.0, chord_tip=1.0, twist=None):
+                 theta0=0.0, chord_root=1.0, chord_tip=1.0, twist=None, kernel="gauss"):
         self.alpha = _d(alpha)
         self.cl = _d(cl)
         self.cd = _d(cd)
@@ -279,6 +293,7 @@ class TurbineSpec:
         t.alpha = _p(self.alpha)
         t.cl = _p(self.cl)
         t.cd = _p(self.cd)
+        t.kernel = KERNEL[kernel]
         self.struct = t
 
     @property
@@ -397,19 +412,20 @@ class Sim:
         return rho[0], u
 
 
-def spread(dom, pos, fblade, eps):
+def spread(dom, pos, fblade, eps, kernel="gauss"):
     pos = _d(pos)
     fb = _d(fblade)
     force = np.zeros((3, dom.nz, dom.ny, dom.nx))
-    lib().or_spread(ctypes.byref(dom), _p(pos), _p(fb), pos.size // 3, float(eps), _p(force))
+    lib().or_spread(ctypes.byref(dom), _p(pos), _p(fb), pos.size // 3, float(eps), KERNEL[kernel], _p(force))
     return force
 
 
-def spread_at(pos, fblade, eps, x, y, z):
+def spread_at(pos, fblade, eps, x, y, z, kernel="gauss"):
     pos = _d(pos)
     fb = _d(fblade)
     out = np.zeros(3)
-    lib().or_spread_at(_p(pos), _p(fb), pos.size // 3, float(eps), int(x), int(y), int(z), _p(out))
+    lib().or_spread_at(_p(pos), _p(fb), pos.size // 3, float(eps), KERNEL[kernel], int(x), int(y), int(z),
+                       _p(out))
     return out
 
 

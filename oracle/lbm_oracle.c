@@ -15,12 +15,14 @@
  *   - blade-line kinematics (Line::update) ................ Sec. 3.3, Algorithm 2
  *   - trilinear interpolation of rho and u ................ Sec. 2.2
  *   - force regularisation f_eps = f (x) eta_eps ........... Sec. 2.2
+ *     (Gaussian kernel, or the discrete delta of Roma et al. 1999 that Sec. 2.2 names)
  *   - blade-element force F = 1/2 rho u_rel^2 w l (...) .... Sec. 2.2, element-force equation
  *   - tabulated polars C_L(alpha), C_D(alpha) ............. Sec. 2.2
  * Readings (paper silent): Gaussian regularisation with per-axis 3*eps cut-off
- * and per-axis renormalisation; lagged force in the velocity sample; Smagorinsky
- * BGK variant (Hou et al. 1996); inlet/outlet/no-slip boundary rules; inflow
- * noise from splitmix64.  Each is stated at its function.
+ * and per-axis renormalisation (the Roma delta needs neither); lagged force in
+ * the velocity sample; Smagorinsky BGK variant (Hou et al. 1996);
+ * inlet/outlet/no-slip boundary rules; inflow noise from splitmix64.  Each is
+ * stated at its function.
  *
  * Velocity ordering: q = (cz+1)*9 + (cy+1)*3 + (cx+1), so q = 13 is the rest
  * population and opposite(q) = 26 - q.  Moment multi-indices (a,b,c) use the
@@ -568,7 +570,10 @@ typedef struct {
     const double* alpha;      /* ascending, radians */
     const double* cl;
     const double* cd;
+    int kernel;               /* OR_KERNEL_GAUSS or OR_KERNEL_ROMA */
 } or_turbine;
+
+enum { OR_KERNEL_GAUSS = 0, OR_KERNEL_ROMA = 1 };
 
 static void matmul3(const double A[3][3], const double B[3][3], double C[3][3])
 {
@@ -773,27 +778,67 @@ double or_gauss_axis_sum(double p, double eps)
     return s;
 }
 
+/*
+ * The discrete delta of Roma, Peskin and Berger (1999), which Sec. 2.2 uses
+ * for the spreading: the three-point function
+ *   phi(r) = (1 + sqrt(1 - 3 r^2)) / 3                  for |r| <= 1/2,
+ *   phi(r) = (5 - 3 |r| - sqrt(1 - 3 (1 - |r|)^2)) / 6   for 1/2 <= |r| <= 3/2,
+ *   phi(r) = 0                                           beyond,
+ * built so that its samples at the integers shifted by any r sum to 1, have
+ * zero first moment and squares summing to 1/2.  The 3-D weight of cell x is
+ * prod_a phi(x_a - p_a); it needs no renormalisation (the conservation Sec. 2.2
+ * notes) and epsilon plays no part.
+ */
+double or_roma_phi(double r)
+{
+    double a = fabs(r);
+    if (a <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * a * a)) / 3.0;
+    if (a <= 1.5) return (5.0 - 3.0 * a - sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a))) / 6.0;
+    return 0.0;
+}
+
+/* Per-axis support [lo, hi] of an element at p: |i - p| <= 3 eps (Gaussian)
+ * or <= 3/2 (Roma). */
+static void support_1d(int kernel, double p, double eps, int* lo, int* hi)
+{
+    double cut = kernel == OR_KERNEL_ROMA ? 1.5 : 3.0 * eps;
+    *lo = (int)ceil(p - cut);
+    *hi = (int)floor(p + cut);
+}
+
+/* Normaliser of an element at p: the product of the Gaussian's axis sums
+ * (1 for Roma). */
+static double reg_norm(int kernel, const double p[3], double eps)
+{
+    if (kernel == OR_KERNEL_ROMA) return 1.0;
+    return or_gauss_axis_sum(p[0], eps) * or_gauss_axis_sum(p[1], eps) * or_gauss_axis_sum(p[2], eps);
+}
+
+/* Regularisation weight of cell c for an element at p with normaliser S. */
+static double reg_weight(int kernel, const double p[3], double eps, double S, const int c[3])
+{
+    double d[3] = {c[0] - p[0], c[1] - p[1], c[2] - p[2]};
+    if (kernel == OR_KERNEL_ROMA) return or_roma_phi(d[0]) * or_roma_phi(d[1]) * or_roma_phi(d[2]);
+    double g = 1.0 / (eps * eps * eps * M_PI * sqrt(M_PI));
+    return g * exp(-(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) / (eps * eps)) / S;
+}
+
 /* Adds -F_k * weight(x) of every element, in element order, to force[3][N].
  * The whole support of every element must lie inside the domain. */
-void or_spread(const or_domain* d, const double* pos, const double* fblade, int n_el, double eps, double* force)
+void or_spread(const or_domain* d, const double* pos, const double* fblade, int n_el, double eps, int kernel,
+               double* force)
 {
     size_t N = (size_t)d->nx * d->ny * d->nz;
     for (int e = 0; e < n_el; ++e) {
         const double* p = pos + 3 * e;
-        double S[3];
-        int lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {
-            S[a] = or_gauss_axis_sum(p[a], eps);
-            lo[a] = (int)ceil(p[a] - 3.0 * eps);
-            hi[a] = (int)floor(p[a] + 3.0 * eps);
-        }
-        for (int z = lo[2]; z <= hi[2]; ++z)
-            for (int y = lo[1]; y <= hi[1]; ++y)
-                for (int x = lo[0]; x <= hi[0]; ++x) {
-                    double dx = x - p[0], dy = y - p[1], dz = z - p[2];
-                    double g = 1.0 / (eps * eps * eps * M_PI * sqrt(M_PI));
-                    double wgt = g * exp(-(dx * dx + dy * dy + dz * dz) / (eps * eps)) / (S[0] * S[1] * S[2]);
-                    size_t ci = cell_index(d, x, y, z);
+        int lo[3], hi[3], c[3];
+        for (int a = 0; a < 3; ++a) support_1d(kernel, p[a], eps, lo + a, hi + a);
+        double S = reg_norm(kernel, p, eps);
+        for (c[2] = lo[2]; c[2] <= hi[2]; ++c[2])
+            for (c[1] = lo[1]; c[1] <= hi[1]; ++c[1])
+                for (c[0] = lo[0]; c[0] <= hi[0]; ++c[0]) {
+                    double wgt = reg_weight(kernel, p, eps, S, c);
+                    size_t ci = cell_index(d, c[0], c[1], c[2]);
                     for (int a = 0; a < 3; ++a) force[(size_t)a * N + ci] += -fblade[3 * e + a] * wgt;
                 }
     }
@@ -801,20 +846,21 @@ void or_spread(const or_domain* d, const double* pos, const double* fblade, int 
 
 /* Spread force at one cell (x, y, z): the same sum as or_spread, restricted to
  * a single cell, in element order. */
-void or_spread_at(const double* pos, const double* fblade, int n_el, double eps, int x, int y, int z, double out[3])
+void or_spread_at(const double* pos, const double* fblade, int n_el, double eps, int kernel, int x, int y, int z,
+                  double out[3])
 {
     out[0] = out[1] = out[2] = 0;
     int c[3] = {x, y, z};
     for (int e = 0; e < n_el; ++e) {
         const double* p = pos + 3 * e;
         int inside = 1;
-        for (int a = 0; a < 3; ++a)
-            if (c[a] < (int)ceil(p[a] - 3.0 * eps) || c[a] > (int)floor(p[a] + 3.0 * eps)) inside = 0;
+        for (int a = 0; a < 3; ++a) {
+            int lo, hi;
+            support_1d(kernel, p[a], eps, &lo, &hi);
+            if (c[a] < lo || c[a] > hi) inside = 0;
+        }
         if (!inside) continue;
-        double S = or_gauss_axis_sum(p[0], eps) * or_gauss_axis_sum(p[1], eps) * or_gauss_axis_sum(p[2], eps);
-        double dx = x - p[0], dy = y - p[1], dz = z - p[2];
-        double g = 1.0 / (eps * eps * eps * M_PI * sqrt(M_PI));
-        double wgt = g * exp(-(dx * dx + dy * dy + dz * dz) / (eps * eps)) / S;
+        double wgt = reg_weight(kernel, p, eps, reg_norm(kernel, p, eps), c);
         for (int a = 0; a < 3; ++a) out[a] += -fblade[3 * e + a] * wgt;
     }
 }
@@ -852,7 +898,7 @@ void or_step_planes(const or_domain* d, const or_turbine* turbs, int n_turb, con
         double* pos = (double*)malloc(sizeof(double) * 3 * ne);
         double* fb = (double*)malloc(sizeof(double) * 3 * ne);
         or_alm_forces(d, t, fsrc, falm_prev, step, pos, fb, NULL, loads + 2 * ti);
-        or_spread(d, pos, fb, ne, t->epsilon, falm_out);
+        or_spread(d, pos, fb, ne, t->epsilon, t->kernel, falm_out);
         if (elem_pos) memcpy(elem_pos + 3 * off, pos, sizeof(double) * 3 * ne);
         if (elem_force) memcpy(elem_force + 3 * off, fb, sizeof(double) * 3 * ne);
         off += ne;

@@ -5,7 +5,8 @@ uniform field against the textbook blade-element split into thrust
 (C_L cos phi + C_D sin phi) and driving force (C_L sin phi - C_D cos phi);
 trilinear sampling against hat-function interpolation of brute-force pulled
 moments; Gaussian spreading against the force-sum identity and the continuous
-Gaussian's unit mass; polar lookup against its nodes.
+Gaussian's unit mass; the Roma delta against the three moment conditions it is
+built from; polar lookup against its nodes.
 """
 import math
 
@@ -18,9 +19,9 @@ from paper_2402_13171_gb300 import inputs as I
 C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
 
 
-def make_turbine(**kw):
+def make_turbine(kernel="gauss", **kw):
     t = I.single_turbine(64, 48, 48, diameter=16.0, hub=(20.0, 24.0, 24.0), elements_per_blade=8, **kw)
-    return O.TurbineSpec(**t), t
+    return O.TurbineSpec(**t, kernel=kernel), t
 
 
 def test_kinematics_circle():
@@ -155,6 +156,67 @@ def test_spread_force_sum_and_support():
         np.testing.assert_allclose(O.spread_at(pos, fb, eps, x, y, z), force[:, z, y, x], atol=1e-15)
 
 
+def _roma_samples(r):
+    """phi(r - j) at every integer j with a non-zero sample."""
+    j = np.arange(math.floor(r) - 3, math.floor(r) + 4)
+    return j, np.array([O.roma_phi(r - jj) for jj in j])
+
+
+def test_roma_delta_moment_conditions():
+    """Roma, Peskin and Berger (1999) construct their three-point delta from
+    three conditions on its integer-shifted samples, for every shift r: they
+    sum to 1, their first moment about r vanishes, and their squares sum to
+    1/2.  A wrong constant, sign or branch breaks at least one of them."""
+    rng = np.random.default_rng(31)
+    for r in np.concatenate([np.linspace(-2.0, 2.0, 81), rng.uniform(-40, 40, 200)]):
+        j, ph = _roma_samples(r)
+        assert np.all(ph >= 0)
+        assert ph.sum() == pytest.approx(1.0, abs=1e-14)
+        assert np.dot(r - j, ph) == pytest.approx(0.0, abs=1e-14)
+        assert np.dot(ph, ph) == pytest.approx(0.5, abs=1e-14)
+        assert np.count_nonzero(ph) <= 3
+
+
+def test_roma_delta_values_and_continuity():
+    assert O.roma_phi(0.0) == pytest.approx(2.0 / 3.0, abs=1e-16)
+    for r in (0.5, -0.5):
+        assert O.roma_phi(r) == pytest.approx(0.5, abs=1e-15)
+    for r in (1.5, -1.5, 1.7, -3.0):
+        assert O.roma_phi(r) == 0.0
+    for r0 in (0.5, 1.5):
+        for dr in (1e-9, 1e-11):
+            assert O.roma_phi(r0 - dr) == pytest.approx(O.roma_phi(r0 + dr), abs=1e-4)
+    for r in np.linspace(0, 1.6, 17):
+        assert O.roma_phi(r) == O.roma_phi(-r)
+
+
+def test_roma_spread_force_sum_centroid_and_support():
+    """With the Roma delta every element's spread force sums to the element
+    force and its force-weighted centroid is the element position (the first
+    moment condition, per axis), with support |x_a - p_a| < 3/2."""
+    d = O.make_domain(24, 24, 24)
+    rng = np.random.default_rng(23)
+    pos = rng.uniform(6, 18, (5, 3))
+    fb = rng.uniform(-1, 1, (5, 3))
+    force = O.spread(d, pos, fb, 2.0, kernel="roma")
+    np.testing.assert_allclose(force.reshape(3, -1).sum(1), -fb.sum(0), atol=1e-14)
+    f1 = O.spread(d, pos[:1], fb[:1], 2.0, kernel="roma")
+    w = f1[0] / -fb[0, 0]
+    assert w.sum() == pytest.approx(1.0, abs=1e-14)
+    zz, yy, xx = np.meshgrid(np.arange(24), np.arange(24), np.arange(24), indexing="ij")
+    for a, g in enumerate((xx, yy, zz)):
+        assert (w * g).sum() == pytest.approx(pos[0, a], abs=1e-12)
+    nz_idx = np.argwhere(w != 0)
+    assert np.all(np.abs(nz_idx[:, ::-1] - pos[0]) < 1.5)
+    assert len(nz_idx) <= 27
+    # epsilon plays no part
+    np.testing.assert_array_equal(O.spread(d, pos, fb, 4.0, kernel="roma"), force)
+    x0, y0, z0 = np.round(pos[0]).astype(int)
+    for (x, y, z) in [(x0, y0, z0), (x0 + 1, y0 - 1, z0), (x0 + 2, y0, z0)]:
+        np.testing.assert_allclose(O.spread_at(pos, fb, 2.0, x, y, z, kernel="roma"), force[:, z, y, x],
+                                   atol=1e-15)
+
+
 def test_polar_lookup():
     a, cl, cd = I.synthetic_polars()
     assert O.table_lookup(a, cl, a[1000]) == cl[1000]
@@ -168,10 +230,11 @@ def test_polar_lookup():
     assert O.table_lookup(a, cd, x) == pytest.approx(0.01 + 0.02 * x * x, abs=0.02 * math.radians(0.1) ** 2)
 
 
-def test_alm_step_momentum_balance():
+@pytest.mark.parametrize("kernel", ["gauss", "roma"])
+def test_alm_step_momentum_balance(kernel):
     """Over one step the fluid momentum changes by exactly minus the sum of the
     blade forces (the spread conserves force)."""
-    s, T, t = uniform_sim(0.05)
+    s, T, t = uniform_sim(0.05, kernel=kernel)
     j0 = np.einsum("qa,qzyx->a", C, s.f)
     s.step(1)
     j1 = np.einsum("qa,qzyx->a", C, s.f)
