@@ -15,6 +15,7 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
   pull streaming + boundaries ..................... periodic shift, bounce-back Poiseuille,
                                                     inlet/outlet constant-state invariance
   blade kinematics, sampling, element forces ...... frozen-field closed form, affine exactness
+  Glauert tip-loss factor ......................... closed-form values, limits, frozen-field loads
   Gaussian spreading .............................. force-sum, separable closed form
   Roma discrete-delta spreading ................... Roma's three moment conditions, force-sum,
                                                     force centroid at the element
@@ -97,6 +98,7 @@ class Turbine(ctypes.Structure):
         ("n_polar", ctypes.c_int),
         ("alpha", _dp), ("cl", _dp), ("cd", _dp),
         ("kernel", ctypes.c_int),
+        ("tip_loss", ctypes.c_int),
     ]
 
 
@@ -133,6 +135,8 @@ def _declare(L):
                                ctypes.c_int, _dp]
     L.or_roma_phi.argtypes = [ctypes.c_double]
     L.or_roma_phi.restype = ctypes.c_double
+    L.or_tip_loss.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.or_tip_loss.restype = ctypes.c_double
     L.or_step.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), ctypes.c_int, _dp, _dp, _dp, _dp, c_long,
                           _dp, _dp, _dp]
     L.or_step_planes.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(Turbine), ctypes.c_int, _dp, _dp, _dp, _dp,
@@ -240,6 +244,11 @@ def roma_phi(r):
     return lib().or_roma_phi(float(r))
 
 
+def tip_loss(n_blades, R, r, phi):
+    """Glauert's tip-loss factor (Prandtl's form) of an element (Sec. 2.2)."""
+    return lib().or_tip_loss(int(n_blades), float(R), float(r), float(phi))
+
+
 # ---------------------------------------------------------------- domain
 
 BC = {"periodic": 0, "inout": 1, "noslip": 2, "freeslip": 3}
@@ -270,7 +279,7 @@ class TurbineSpec:
     """Owns the numpy arrays an oracle Turbine struct points into."""
 
     def __init__(self, hub, radius, n_blades, n_elements, epsilon, omega, alpha, cl, cd, yaw=0.0, pitch=0.0,
-                 theta0=0.0, chord_root=1.0, chord_tip=1.0, twist=None, kernel="gauss"):
+                 theta0=0.0, chord_root=1.0, chord_tip=1.0, twist=None, kernel="gauss", tip_loss=False):
         self.alpha = _d(alpha)
         self.cl = _d(cl)
         self.cd = _d(cd)
@@ -294,6 +303,7 @@ class TurbineSpec:
         t.cl = _p(self.cl)
         t.cd = _p(self.cd)
         t.kernel = KERNEL[kernel]
+        t.tip_loss = int(bool(tip_loss))
         self.struct = t
 
     @property

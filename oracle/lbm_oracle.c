@@ -18,6 +18,7 @@
  *     (Gaussian kernel, or the discrete delta of Roma et al. 1999 that Sec. 2.2 names)
  *   - blade-element force F = 1/2 rho u_rel^2 w l (...) .... Sec. 2.2, element-force equation
  *   - tabulated polars C_L(alpha), C_D(alpha) ............. Sec. 2.2
+ *   - Glauert tip-loss factor (optional) .................. Sec. 2.2, Sec. 5
  * Readings (paper silent): Gaussian regularisation with per-axis 3*eps cut-off
  * and per-axis renormalisation (the Roma delta needs neither); lagged force in
  * the velocity sample; Smagorinsky BGK variant (Hou et al. 1996);
@@ -571,6 +572,7 @@ typedef struct {
     const double* cl;
     const double* cd;
     int kernel;               /* OR_KERNEL_GAUSS or OR_KERNEL_ROMA */
+    int tip_loss;             /* 1: Glauert tip-loss factor on the element forces */
 } or_turbine;
 
 enum { OR_KERNEL_GAUSS = 0, OR_KERNEL_ROMA = 1 };
@@ -703,15 +705,33 @@ void or_sample(const or_domain* d, const double* fsrc, const double* force_prev,
 }
 
 /*
+ * Glauert's tip-loss factor (Sec. 2.2 names tip-loss models as an option of
+ * the actuator line; the validation of Sec. 5 turns the Glauert type off),
+ * in Prandtl's form: for B blades of radius R, an element at radius r and
+ * inflow angle phi,
+ *   F = (2/pi) arccos(exp(-B (R - r) / (2 r |sin phi|))),
+ * the factor on the element force.  F -> 1 as sin phi -> 0 (the exponent's
+ * limit), and F = 0 at the tip.
+ */
+double or_tip_loss(int n_blades, double R, double r, double phi)
+{
+    double s = fabs(sin(phi));
+    if (s == 0.0) return 1.0;
+    double f = n_blades * (R - r) / (2.0 * r * s);
+    return 2.0 / M_PI * acos(exp(-f));
+}
+
+/*
  * Blade-element forces (Sec. 2.2): with u sampled at the element, the
  * relative velocity u_rel = u - v has its radial part removed; the inflow
  * angle is phi = atan2(u_rel.e_axis, -u_rel.e_t) and alpha = phi - twist -
  * pitch.  C_L, C_D come from the tables; e_D = u_rel/|u_rel|, e_L = e_D x e_r;
  * F_blade = 1/2 rho |u_rel|^2 c l (C_L e_L + C_D e_D) with chord c(r) varying
  * linearly from root to tip and l = R / N_e.  The force on the fluid is
- * -F_blade.  Thrust = sum F_blade . e_axis, torque = sum ((p-hub) x F_blade) .
- * e_axis.  Outputs per element (blade-major): pos, F_blade, alpha, and the
- * two rotor loads.
+ * -F_blade.  With the tip-loss option F_blade is scaled by or_tip_loss.
+ * Thrust = sum F_blade . e_axis, torque = sum ((p-hub) x F_blade) . e_axis.
+ * Outputs per element (blade-major): pos, F_blade, alpha, and the two rotor
+ * loads.
  */
 void or_alm_forces(const or_domain* d, const or_turbine* t, const double* fsrc, const double* force_prev, long step,
                    double* pos_out, double* force_out, double* alpha_out, double loads[2])
@@ -744,6 +764,7 @@ void or_alm_forces(const or_domain* d, const or_turbine* t, const double* fsrc, 
                 double eD[3] = {ur[0] / mag, ur[1] / mag, ur[2] / mag};
                 double eL[3] = {eD[1] * er[2] - eD[2] * er[1], eD[2] * er[0] - eD[0] * er[2], eD[0] * er[1] - eD[1] * er[0]};
                 double s = 0.5 * rho * mag2 * chord * len;
+                if (t->tip_loss) s *= or_tip_loss(t->n_blades, t->radius, r, phi);
                 for (int a = 0; a < 3; ++a) Fb[a] = s * (CL * eL[a] + CD * eD[a]);
             }
             double rel[3] = {p[0] - t->hub[0], p[1] - t->hub[1], p[2] - t->hub[2]};

@@ -89,17 +89,20 @@ def synthetic_polars(step_deg=0.1, cl_slope=2 * math.pi, cl_max=1.2, cd0=0.01, c
 
 
 def single_turbine(nx=256, ny=128, nz=128, diameter=32.0, hub=None, elements_per_blade=40, epsilon=2.0,
-                   tsr=6.0, u_inf=0.05, chord_root=2.0, chord_tip=1.0, n_blades=3, yaw=0.0):
+                   tsr=6.0, u_inf=0.05, chord_root=2.0, chord_tip=1.0, n_blades=3, yaw=0.0, kernel="gauss",
+                   tip_loss=False):
     """The single three-bladed rotor of the 256x128x128 actuator-line workload:
     D = 32 cells at (64, 64, 64), 40 elements per blade, eps = 2, TSR 6 at
-    U = 0.05, chord 2 -> 1.  Rotor speed omega = TSR U / R (rad per step)."""
+    U = 0.05, chord 2 -> 1.  Rotor speed omega = TSR U / R (rad per step).
+    kernel: force regularisation, "gauss" (width epsilon) or "roma";
+    tip_loss: Glauert's tip-loss factor on the element forces."""
     R = diameter / 2.0
     if hub is None:
         hub = (nx / 4.0, ny / 2.0, nz / 2.0)
     alpha, cl, cd = synthetic_polars()
     return dict(hub=tuple(float(h) for h in hub), radius=R, n_blades=n_blades, n_elements=elements_per_blade,
                 epsilon=epsilon, omega=tsr * u_inf / R, yaw=yaw, pitch=0.0, theta0=0.0, chord_root=chord_root,
-                chord_tip=chord_tip, alpha=alpha, cl=cl, cd=cd)
+                chord_tip=chord_tip, alpha=alpha, cl=cl, cd=cd, kernel=kernel, tip_loss=tip_loss)
 
 
 def single_turbine_case(nx=256, ny=128, nz=128, **kw):

@@ -19,9 +19,9 @@ from paper_2402_13171_gb300 import inputs as I
 C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
 
 
-def make_turbine(kernel="gauss", **kw):
+def make_turbine(**kw):
     t = I.single_turbine(64, 48, 48, diameter=16.0, hub=(20.0, 24.0, 24.0), elements_per_blade=8, **kw)
-    return O.TurbineSpec(**t, kernel=kernel), t
+    return O.TurbineSpec(**t), t
 
 
 def test_kinematics_circle():
@@ -84,6 +84,50 @@ def test_frozen_field_blade_element_forces():
     assert loads[0] == pytest.approx(thrust, rel=1e-10)
     assert loads[1] == pytest.approx(torque, rel=1e-10)
     assert loads[0] > 0 and loads[1] > 0   # thrust downstream, driving torque
+
+
+def test_tip_loss_factor_values_and_limits():
+    """Glauert's tip-loss factor in Prandtl's form, F = (2/pi) arccos(e^-f),
+    f = B (R - r) / (2 r |sin phi|): F = 2/3 where f = ln 2 (arccos 1/2 =
+    pi/3), F = 1/2 where e^-f = cos(pi/4); F = 0 at the tip, F -> 1 far
+    inboard or for sin phi -> 0, even in phi, rising with the blade count."""
+    B, R = 3, 16.0
+    # choose r so that f = ln 2 at phi = 0.3
+    phi = 0.3
+    r = B * R / (B + 2 * math.log(2) * math.sin(phi))
+    assert O.tip_loss(B, R, r, phi) == pytest.approx(2.0 / 3.0, abs=1e-14)
+    f = -math.log(math.cos(math.pi / 4))
+    r = B * R / (B + 2 * f * math.sin(phi))
+    assert O.tip_loss(B, R, r, phi) == pytest.approx(0.5, abs=1e-14)
+    assert O.tip_loss(B, R, R, phi) == 0.0
+    assert O.tip_loss(B, R, 0.5, phi) == pytest.approx(1.0, abs=1e-12)
+    assert O.tip_loss(B, R, 15.0, 0.0) == 1.0
+    assert O.tip_loss(B, R, 15.0, 1e-9) == pytest.approx(1.0, abs=1e-12)
+    for rr in (4.0, 12.0, 15.5):
+        assert O.tip_loss(B, R, rr, -phi) == O.tip_loss(B, R, rr, phi)
+        assert O.tip_loss(2, R, rr, phi) < O.tip_loss(3, R, rr, phi) < O.tip_loss(6, R, rr, phi)
+    Fs = [O.tip_loss(B, R, rr, phi) for rr in np.linspace(1.0, R, 40)]
+    assert all(a >= b for a, b in zip(Fs, Fs[1:]))
+
+
+def test_frozen_field_tip_loss_scales_each_element():
+    """In a frozen uniform field the tip-loss option multiplies each element
+    force by its factor at the element's inflow angle and nothing else, and it
+    takes thrust and torque down."""
+    U = 0.05
+    s0, _, t = uniform_sim(U)
+    s1, _, _ = uniform_sim(U, tip_loss=True)
+    pos0, fb0, alpha0, loads0 = s0.alm_forces(s0.f, s0.falm, 0)
+    pos1, fb1, alpha1, loads1 = s1.alm_forces(s1.f, s1.falm, 0)
+    np.testing.assert_array_equal(alpha0, alpha1)
+    R, ne = t["radius"], t["n_elements"]
+    for e in range(fb0.shape[0]):
+        r = (e % ne + 0.5) * R / ne
+        F = O.tip_loss(3, R, r, alpha0[e])
+        np.testing.assert_allclose(fb1[e], F * fb0[e], rtol=1e-13, atol=1e-18)
+    assert fb1[ne - 1, 0] < 0.7 * fb0[ne - 1, 0]      # outermost element loses most
+    assert fb1[0, 0] > 0.99 * fb0[0, 0]               # innermost hardly at all
+    assert 0 < loads1[0] < loads0[0] and 0 < loads1[1] < loads0[1]
 
 
 def test_sampling_is_hat_interpolation_of_pulled_moments():
