@@ -50,6 +50,9 @@ def parse_args():
                         "tilesweep: the single-rotor workload at every tile candidate of the tuner")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--kernel", choices=["gauss", "roma"], default="gauss",
+                   help="force regularisation of the single-rotor workload: the Gaussian (eps = 2) or Roma's "
+                        "three-point delta")
     return p.parse_args()
 
 
@@ -336,7 +339,7 @@ def run_ours(args):
 
     tile = (0, 0, 0, 0) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
     if args.workload == "single":
-        dom, turb = I.single_turbine_case()
+        dom, turb = I.single_turbine_case(kernel=args.kernel)
         dom["collision"] = args.collision
         lat = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], device=local, collision=args.collision,
                                  nu=dom["nu"], smag_c=dom["smag_c"], storage=args.storage, bc=dom["bc"],
@@ -344,8 +347,9 @@ def run_ours(args):
         lat.set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
         lat.add_turbine(**turb)
         lattices = [lat]
-        workload = WORKLOAD
-        extra = {"rotor": "3 blades x 40 elements, D=32 at (64,64,64), eps=2, TSR 6"}
+        workload = WORKLOAD if args.kernel == "gauss" else WORKLOAD + "_roma"
+        extra = {"rotor": "3 blades x 40 elements, D=32 at (64,64,64), TSR 6, "
+                          + ("Gaussian eps=2" if args.kernel == "gauss" else "Roma 3-point delta")}
     else:
         cases = I.batch_instances(16)
         cfgs = [dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], collision=args.collision, nu=d["nu"], smag_c=d["smag_c"],
@@ -367,8 +371,9 @@ def run_ours(args):
     bytes_per_cell, cells = lat.traffic_model()
     lat.step(args.warmup)
     lat.sync()
+    launches_per_step = lat.launches_per_step()
 
-    # ---- timed region: K launches, CUDA events on the launch stream, per-kernel events inside
+    # ---- timed region: K steps, CUDA events on the launch stream, per-replay events inside
     clocks = ClockSampler(local)
     lat.set_profiling(True)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -383,7 +388,7 @@ def run_ours(args):
     clk = clocks.stop()
     lat.sync()
     elapsed_ms = e0.elapsed_time(e1)
-    kernel_ms, launches = lat.kernel_time()
+    kernel_ms, timed_steps = lat.kernel_time()
     lat.set_profiling(False)
     elapsed_ms, kernel_ms = reduce_max([elapsed_ms, kernel_ms], dist, device="cuda")
     value = job_mlups(world, cells, args.steps, elapsed_ms)
@@ -399,12 +404,22 @@ def run_ours(args):
         rho_h = torch.ones(N, dtype=torch.float64).pin_memory().numpy()
         u_h = torch.zeros(3 * N, dtype=torch.float64).pin_memory().numpy()
         u_h[:N] = dom["u_ref"][0]
+        # each step's loads land in page-locked memory and are read one step
+        # behind, so the host never waits on the step it has just enqueued
+        loads_h = torch.empty((2, 2), dtype=torch.float64).pin_memory()
+        evs = [torch.cuda.Event(), torch.cuda.Event()]
         barrier()
         t = time.perf_counter()
         lat.init_fields(rho_h, u_h)
-        for _ in range(args.steps):
+        for i in range(args.steps):
             lat.step(1)
-            lat.loads(0)
+            lat.loads_async(loads_h[i % 2])
+            evs[i % 2].record(lat.stream)
+            if i > 0:
+                evs[(i - 1) % 2].synchronize()
+                thrust_e2e = loads_h[(i - 1) % 2].tolist()
+        evs[(args.steps - 1) % 2].synchronize()
+        thrust_e2e = loads_h[(args.steps - 1) % 2].tolist()
         rho_o, u_o = lat.moments()
         barrier()
         dt = time.perf_counter() - t
@@ -412,7 +427,9 @@ def run_ours(args):
         e2e = {"value": job_mlups(world, cells, args.steps, dt * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": 16.0 * N / args.steps,
                "d2h_bytes_per_step": 16.0 + 32.0 * N / args.steps,
-               "api": "lbm_init_fields(host rho, u) + K x (lbm_step(1) + alm_get_loads) + lbm_get_moments"}
+               "api": "lbm_init_fields(host rho, u) + K x (lbm_step(1) + alm_get_loads_async into page-locked "
+                      "memory, read one step behind) + lbm_get_moments",
+               "last_loads": thrust_e2e}
 
     acc = None
     cpu = None
@@ -446,7 +463,7 @@ def run_ours(args):
                          "kernel": "k_step (fused stream-collide + in-kernel ALM)",
                          "bytes_per_cell": bytes_per_cell, "kernel_ms": kernel_ms, "peak_kind": peak_kind},
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clk,
             "cpu_baseline": cpu,
             "accuracy": {"max_du_vs_fp64_oracle": acc, "case": "48x32x32 rotor, 50 steps"} if acc is not None else None,
@@ -641,8 +658,8 @@ TILE_CANDIDATES = [(32, 4, 1, 0), (32, 2, 1, 0), (32, 8, 1, 0), (64, 2, 1, 0), (
 
 def run_tilesweep(args):
     """The single-rotor workload at every tile candidate of the tuner: the
-    k_step time per launch (CUDA events over --steps launches after --warmup)
-    and its fraction of the HBM roofline.  Under `ncu --metrics
+    k_step device time per step (CUDA events over --steps steps after
+    --warmup) and its fraction of the HBM roofline.  Under `ncu --metrics
     dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_step` it gives the
     DRAM bytes of every tile in one pass."""
     import torch

@@ -7,7 +7,7 @@
  *   2. trilinear sampling of rho and u at every blade element (Sec. 2.2);
  *   3. blade-element forces from tabulated polars (Sec. 2.2, element-force equation);
  *   4. regularisation of the element forces onto the lattice, f_eps = f (x) eta_eps (Sec. 2.2),
- *      with a Gaussian kernel;
+ *      with a Gaussian kernel or the discrete delta of Roma et al. (1999) the paper uses;
  *   5. pull streaming with boundary rules, and
  *   6. cumulant collision (Geier et al. 2015, Sec. 2.1) or BGK-Smagorinsky with Guo forcing
  *      (Sec. 2.1, lattice Boltzmann equation with source term).
@@ -103,13 +103,24 @@ typedef struct {
  * (k + 1/2) R / n_elements, length R / n_elements, chord linear from
  * chord_root (r = 0) to chord_tip (r = R); alpha = phi - twist_k - pitch.
  * The polar table (alpha ascending, radians) is interpolated linearly and
- * clamped at its ends.  The whole force support (hub +- (R + 3 eps + 1)) must
- * lie inside [1, n-2] on every axis, and epsilon must be in [0.5, 5]. */
+ * clamped at its ends.  The force of element k is spread with the kernel
+ * `regularisation` names:
+ *   ALM_REG_GAUSSIAN: prod_a exp(-d_a^2 / eps^2) on |d_a| <= 3 eps, each axis
+ *     renormalised to unit lattice sum (eps in [0.5, 5]);
+ *   ALM_REG_ROMA: prod_a phi(d_a), Roma, Peskin and Berger's three-point
+ *     delta on |d_a| <= 3/2, unit sum by construction (epsilon unused),
+ * d = cell - element position.  With tip_loss = 1 each element force is
+ * scaled by Glauert's tip-loss factor in Prandtl's form (Sec. 2.2),
+ * F = (2/pi) arccos(exp(-B (R - r) / (2 r |sin phi|))), phi the inflow angle
+ * (F = 1 where sin phi = 0).  The whole force support (hub +- (R + cut + 1),
+ * cut = 3 eps or 3/2) must lie inside [1, n-2] on every axis. */
+typedef enum { ALM_REG_GAUSSIAN = 0, ALM_REG_ROMA = 1 } alm_regularisation;
+
 typedef struct {
     double hub[3];
     double radius;
     int n_blades, n_elements;
-    double epsilon;       /* Gaussian width, cells */
+    double epsilon;       /* Gaussian width, cells (ALM_REG_GAUSSIAN) */
     double omega;         /* rotor speed, rad per step, positive about the axis */
     double yaw, pitch, theta0;
     double chord_root, chord_tip;
@@ -118,6 +129,8 @@ typedef struct {
     const double* alpha;
     const double* cl;
     const double* cd;
+    int regularisation;   /* alm_regularisation; 0 (zero-initialised) = Gaussian */
+    int tip_loss;         /* 1: Glauert tip-loss factor on the element forces, 0: none */
 } alm_turbine_desc;
 
 /* Create one lattice.  The state starts at f = feq(rho = 1, u = 0) until
@@ -144,8 +157,9 @@ lbm_status lbm_set_inflow(lbm_ctx* ctx, const lbm_inflow* inflow);
 lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, const float* fneq);
 
 /* Add a rotor (copied).  id_out receives its index within this lattice.
- * Errors: INVALID_ARG for a support outside [1, n-2], bad epsilon, table or
- * element counts (at most 4096 elements per lattice). */
+ * Errors: INVALID_ARG for a support outside [1, n-2], an unknown
+ * regularisation or tip_loss code, bad epsilon (Gaussian), table or element
+ * counts (at most 4096 elements per lattice). */
 lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* desc, int* id_out);
 
 /* Enqueue n_steps time steps on the stream: replays of captured 8- and 2-step
@@ -178,6 +192,16 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f);
  * (3 floats each, blade-major).  Synchronises. */
 lbm_status alm_get_loads(lbm_ctx* ctx, int id, double* thrust, double* torque, float* elem_force, float* elem_pos);
 
+/* The same thrust and torque, without waiting: enqueues a copy of the 2
+ * doubles of the last enqueued step into thrust_torque on the lattice's
+ * stream and returns.  thrust_torque (host, caller-owned) must stay valid
+ * until the stream has passed the copy (lbm_sync, or an event the caller
+ * records on the stream); from page-locked memory the copy is asynchronous,
+ * so a serving loop can enqueue step n + 1 before it reads the loads of step
+ * n.  Device errors surface at the next synchronising call.  Errors:
+ * INVALID_ARG for a bad rotor id or a null output. */
+lbm_status alm_get_loads_async(lbm_ctx* ctx, int id, double* thrust_torque);
+
 /* FP64 sums [mass, momentum x, y, z] of the last diagnostic step (post-
  * collision state).  Synchronises; NUMERIC if NaN/Inf was seen. */
 lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_step);
@@ -208,16 +232,22 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
                         double* best_ms);
 
 /* Kernel timing: when enabled, lbm_step brackets every replay of its 8- or
- * 2-step graph (or a single step launch) with CUDA events on the lattice's stream, so
+ * 2-step graph (or a single step) with CUDA events on the lattice's stream, so
  * timing does not break up the replays; lbm_get_kernel_time returns the mean
- * duration per step launch (ms) and the number of timed launches since
- * enabling. */
+ * device time per time step (ms, both launches of a step) and the number of
+ * timed steps since enabling. */
 lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable);
-lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches);
+lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* steps);
 
 /* Algorithmic bytes one time step moves per cell (27 loads + 27 stores of
  * the storage type) and the number of cells of one step (all lattices). */
-lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_launch);
+lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_step);
+
+/* Kernel launches of one time step with the current tile and rotors: 2 (the
+ * tiles around the rotors, then the rest) or 1 (staged rows, or a lattice
+ * without rotor tiles).  Uploads pending descriptors first (stream-ordered).
+ * Errors: INVALID_ARG for a null output. */
+lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches);
 
 /* Actuator-line evaluation for callers that cannot allocate device memory:
  * a real-time turbine-controller loop, or code embedded in another framework

@@ -580,7 +580,12 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     if ((int)I.turb.size() >= kMaxTurbines) return fail(b, LBM_ERR_INVALID_ARG, "too many rotors", false);
     if (d->n_blades < 1 || d->n_elements < 1 || I.h.n_el + d->n_blades * d->n_elements > kMaxElements)
         return fail(b, LBM_ERR_INVALID_ARG, "element count out of range", false);
-    if (!(d->epsilon >= 0.5 && d->epsilon <= 5.0)) return fail(b, LBM_ERR_INVALID_ARG, "epsilon must be in [0.5, 5]", false);
+    if (d->regularisation != ALM_REG_GAUSSIAN && d->regularisation != ALM_REG_ROMA)
+        return fail(b, LBM_ERR_INVALID_ARG, "unknown regularisation", false);
+    if (d->tip_loss != 0 && d->tip_loss != 1) return fail(b, LBM_ERR_INVALID_ARG, "tip_loss must be 0 or 1", false);
+    const bool roma = d->regularisation == ALM_REG_ROMA;
+    if (!roma && !(d->epsilon >= 0.5 && d->epsilon <= 5.0))
+        return fail(b, LBM_ERR_INVALID_ARG, "epsilon must be in [0.5, 5]", false);
     if (!(d->radius > 0.0)) return fail(b, LBM_ERR_INVALID_ARG, "radius must be > 0", false);
     if (d->n_polar < 2 || !d->alpha || !d->cl || !d->cd) return fail(b, LBM_ERR_INVALID_ARG, "polar table missing", false);
     for (int i = 1; i < d->n_polar; ++i)
@@ -595,7 +600,7 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     const double cy = std::cos(d->yaw), sy = std::sin(d->yaw);
     const double ea[3] = {cy, sy, 0.0}, e1[3] = {-sy, cy, 0.0}, e2[3] = {0.0, 0.0, 1.0};
     const int n[3] = {I.h.nx, I.h.ny, I.h.nz};
-    const double cut = 3.0 * d->epsilon;
+    const double cut = roma ? 1.5 : 3.0 * d->epsilon;
     for (int a = 0; a < 3; ++a) {
         B.hub[a] = (float)d->hub[a];
         B.e_axis[a] = (float)ea[a];
@@ -610,9 +615,11 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     B.radius = (float)d->radius;
     B.n_blades = d->n_blades;
     B.n_elements = d->n_elements;
-    B.eps = (float)d->epsilon;
-    B.inv_eps2 = (float)(1.0 / (d->epsilon * d->epsilon));
+    B.eps = roma ? 0.0f : (float)d->epsilon;
+    B.inv_eps2 = roma ? 0.0f : (float)(1.0 / (d->epsilon * d->epsilon));
     B.cut = (float)cut;
+    B.roma = roma ? 1 : 0;
+    B.tip_loss = d->tip_loss;
     B.omega = d->omega;
     B.theta0 = d->theta0;
     B.pitch = (float)d->pitch;
@@ -907,6 +914,19 @@ lbm_status alm_get_loads(lbm_ctx* ctx, int id, double* thrust, double* torque, f
     return LBM_OK;
 }
 
+lbm_status alm_get_loads_async(lbm_ctx* ctx, int id, double* thrust_torque)
+{
+    ENTER(ctx);
+    if (id < 0 || id >= (int)I.turb.size()) return fail(b, LBM_ERR_INVALID_ARG, "bad rotor id", false);
+    if (!thrust_torque) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    // the slot of the last enqueued step; the next step's rotor launch, which
+    // rewrites it, is ordered after this copy on the stream
+    const int par = b->host_step > 0 ? (int)((b->host_step - 1) & 1) : 0;
+    CK(cudaMemcpyAsync(thrust_torque, I.h.loads[par] + 2 * id, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       b->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_step)
 {
     ENTER(ctx);
@@ -1151,23 +1171,34 @@ lbm_status lbm_set_profiling(lbm_ctx* ctx, int enable)
     return LBM_OK;
 }
 
-lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* launches)
+lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* steps)
 {
     ENTER(ctx);
     lbm_status s = fold_events(b);
     if (s != LBM_OK) return s;
     if (mean_ms) *mean_ms = b->prof_n ? b->prof_ms / (double)b->prof_n : 0.0;
-    if (launches) *launches = b->prof_n;
+    if (steps) *steps = b->prof_n;
     return LBM_OK;
 }
 
-lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_launch)
+lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_step)
 {
     ENTER(ctx);
     if (bytes_per_cell) *bytes_per_cell = 54.0 * (double)store_bytes(b->store);
     long long cells = 0;
     for (auto& In : b->inst) cells += In.h.N;
-    if (cells_per_launch) *cells_per_launch = cells;
+    if (cells_per_step) *cells_per_step = cells;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
+{
+    ENTER(ctx);
+    if (!launches) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    // the same split as launch_one
+    *launches = b->staged ? 1 : (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
     return LBM_OK;
 }
 

@@ -25,7 +25,9 @@ struct DevTurbine {
     float hub[3];
     float radius;
     int n_blades, n_elements;
-    float eps, inv_eps2, cut;  // Gaussian width, 1/eps^2, cut-off 3 eps
+    float eps, inv_eps2, cut;  // Gaussian width, 1/eps^2, per-axis cut-off (3 eps, or 3/2 for Roma)
+    int roma;                  // 1: Roma three-point delta, 0: Gaussian
+    int tip_loss;              // 1: Glauert tip-loss factor on the element forces
     double omega, theta0;      // rad per step, rad
     float e_axis[3], e1[3], e2[3];
     float pitch, chord_root, chord_tip;

@@ -2,7 +2,7 @@
 //
 // k_step: the fused pass of a time step over every cell of every lattice of a
 // batch: pull streaming with boundary rules (Sec. 2.1, streaming step), force
-// (body force + Gaussian-regularised blade forces, Sec. 2.2, gathered in the
+// (body force + regularised blade forces, Sec. 2.2, gathered in the
 // rotor box), collision (cumulant, Sec. 2.1 / Geier et al. 2015, or BGK with a
 // Smagorinsky eddy viscosity), store.  PDFs live in HBM as offsets h = f - w
 // in the storage type; all arithmetic is FP32.  A step is two launches: the
@@ -559,6 +559,31 @@ __device__ __forceinline__ void element_geometry(const DevDomain* D, int g, long
     }
 }
 
+// Three-point discrete delta of Roma, Peskin and Berger (1999), the spreading
+// kernel of Sec. 2.2: (1 + sqrt(1 - 3 r^2)) / 3 for |r| <= 1/2,
+// (5 - 3|r| - sqrt(1 - 3 (1 - |r|)^2)) / 6 for 1/2 < |r| <= 3/2, else 0.
+__device__ __forceinline__ float roma_phi(float r)
+{
+    const float a = fabsf(r);
+    if (a <= 0.5f) return (1.0f + sqrtf(1.0f - 3.0f * a * a)) * (1.0f / 3.0f);
+    if (a <= 1.5f) {
+        const float b = 1.0f - a;
+        return (5.0f - 3.0f * a - sqrtf(fmaxf(1.0f - 3.0f * b * b, 0.0f))) * (1.0f / 6.0f);
+    }
+    return 0.0f;
+}
+
+// Glauert's tip-loss factor in Prandtl's form (Sec. 2.2): for B blades of
+// radius R, an element at radius r with inflow angle phi,
+// (2/pi) arccos(exp(-B (R - r) / (2 r |sin phi|))); 1 where sin phi = 0.
+__device__ __forceinline__ float tip_loss_factor(int n_blades, float R, float r, float phi)
+{
+    const float s = fabsf(sinf(phi));
+    if (s == 0.0f) return 1.0f;
+    const float f = (float)n_blades * (R - r) / (2.0f * r * s);
+    return 0.63661977f * acosf(expf(-f));  // 2/pi
+}
+
 // Actuator line of step `step` for one lattice, by the whole CTA.  Reads the
 // populations of the current array f (post-collision of step-1) and the box
 // force of step-1; writes element positions with their spreading
@@ -567,7 +592,8 @@ __device__ __forceinline__ void element_geometry(const DevDomain* D, int g, long
 //  phase 1, one thread per (element, corner): pull the 27 populations of the
 //    corner cell, rho and u = (sum c f + F/2)/rho at the corner;
 //  phase 2, one thread per element: trilinear blend, relative velocity,
-//    angle of attack, polars, blade force, Gaussian normalisation, FP64 loads;
+//    angle of attack, polars, blade force (with the tip-loss factor if set),
+//    kernel normalisation, FP64 loads;
 //  phase 3, warp 0: per-rotor FP64 sums in a fixed order.
 template <typename T>
 __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long long step)
@@ -652,19 +678,25 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
             const float eD[3] = {ur[0] / mag, ur[1] / mag, ur[2] / mag};
             const float eL[3] = {eD[1] * G.er[2] - eD[2] * G.er[1], eD[2] * G.er[0] - eD[0] * G.er[2],
                                  eD[0] * G.er[1] - eD[1] * G.er[0]};
-            const float sc = 0.5f * rho_p * mag2 * chord * G.len;
+            float sc = 0.5f * rho_p * mag2 * chord * G.len;
+            if (B->tip_loss) sc *= tip_loss_factor(B->n_blades, B->radius, G.r, phi);
 #pragma unroll
             for (int a = 0; a < 3; ++a) Fb[a] = sc * (CL * eL[a] + CD * eD[a]);
         }
-        // Gaussian normalisation: per-axis sums of exp(-(i - p)^2 / eps^2) over |i - p| <= 3 eps
+        // normalisation: per-axis sums of the kernel's weights over |i - p| <= cut
+        // (exp(-(i - p)^2 / eps^2) for the Gaussian; 1 up to rounding for Roma)
         float S = 1.0f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int lo = (int)ceilf(G.p[a] - B->cut), hi = (int)floorf(G.p[a] + B->cut);
             float sa = 0.0f;
-            for (int i = lo; i <= hi; ++i) {
-                const float d = (float)i - G.p[a];
-                sa += expf(-d * d * B->inv_eps2);
+            if (B->roma) {
+                for (int i = lo; i <= hi; ++i) sa += roma_phi((float)i - G.p[a]);
+            } else {
+                for (int i = lo; i <= hi; ++i) {
+                    const float d = (float)i - G.p[a];
+                    sa += expf(-d * d * B->inv_eps2);
+                }
             }
             S *= sa;
         }
@@ -775,9 +807,39 @@ __device__ __forceinline__ void load_cell(const DevDomain* D, const T* __restric
     }
 }
 
-// Gaussian-regularised blade force at cell (x, y, z) of a rotor tile, summed
-// over the rotors whose box holds the cell (element order; from the culled
-// list when it fits); each rotor's part is stored in its force box.
+// Regularised force of rotor t at cell (x, y, z): the sum over its elements in
+// element order (from the culled list when it fits) of -w F_e, with w the
+// Gaussian exp(-|d|^2 / eps^2) (ROMA false) or the product of Roma's delta
+// (ROMA true) times the element's normaliser.  The kernel is a template
+// argument so that the pair loop carries no per-pair branch on it.
+template <bool ROMA>
+__device__ __forceinline__ void gather_rotor(const DevTurbine* B, int t, int x, int y, int z, int n_cull,
+                                             const float4* s_pos, const float4* s_frc, const int* s_tag,
+                                             const float4* P, const float4* Fe, float& ax, float& ay, float& az)
+{
+    const float cut = B->cut, ie2 = B->inv_eps2;
+    auto add = [&](float4 pe, float4 fe_or_none, bool from_list, int e) {
+        const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
+        if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
+            const float w = (ROMA ? roma_phi(dx) * roma_phi(dy) * roma_phi(dz)
+                                  : expf(-(dx * dx + dy * dy + dz * dz) * ie2)) * pe.w;
+            const float4 fe = from_list ? fe_or_none : __ldg(Fe + B->el_offset + e);
+            ax -= w * fe.x;
+            ay -= w * fe.y;
+            az -= w * fe.z;
+        }
+    };
+    if (n_cull >= 0) {
+        for (int i = 0; i < n_cull; ++i)
+            if (s_tag[i] == t) add(s_pos[i], s_frc[i], true, 0);
+    } else {
+        const int ne = B->n_blades * B->n_elements;
+        for (int e = 0; e < ne; ++e) add(__ldg(P + B->el_offset + e), make_float4(0.f, 0.f, 0.f, 0.f), false, e);
+    }
+}
+
+// Regularised blade force at cell (x, y, z) of a rotor tile, summed over the
+// rotors whose box holds the cell; each rotor's part is stored in its force box.
 __device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, int x, int y, int z, int n_cull,
                                             const float4* s_pos, const float4* s_frc, const int* s_tag, float F[3])
 {
@@ -786,35 +848,11 @@ __device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, 
     for (int t = 0; t < D->n_turb; ++t) {
         const DevTurbine* B = D->turb + t;
         if (x < B->lo[0] || x > B->hi[0] || y < B->lo[1] || y > B->hi[1] || z < B->lo[2] || z > B->hi[2]) continue;
-        const int ne = B->n_blades * B->n_elements;
-        const float cut = B->cut, ie2 = B->inv_eps2;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        if (n_cull >= 0) {
-            for (int i = 0; i < n_cull; ++i) {
-                if (s_tag[i] != t) continue;
-                const float4 pe = s_pos[i];
-                const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
-                if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
-                    const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
-                    const float4 fe = s_frc[i];
-                    ax -= w * fe.x;
-                    ay -= w * fe.y;
-                    az -= w * fe.z;
-                }
-            }
-        } else {
-            for (int e = 0; e < ne; ++e) {
-                const float4 pe = __ldg(P + B->el_offset + e);
-                const float dx = (float)x - pe.x, dy = (float)y - pe.y, dz = (float)z - pe.z;
-                if (fabsf(dx) <= cut && fabsf(dy) <= cut && fabsf(dz) <= cut) {
-                    const float w = expf(-(dx * dx + dy * dy + dz * dz) * ie2) * pe.w;
-                    const float4 fe = __ldg(Fe + B->el_offset + e);
-                    ax -= w * fe.x;
-                    ay -= w * fe.y;
-                    az -= w * fe.z;
-                }
-            }
-        }
+        if (B->roma)
+            gather_rotor<true>(B, t, x, y, z, n_cull, s_pos, s_frc, s_tag, P, Fe, ax, ay, az);
+        else
+            gather_rotor<false>(B, t, x, y, z, n_cull, s_pos, s_frc, s_tag, P, Fe, ax, ay, az);
         const long long bi = ((long long)(z - B->lo[2]) * B->bny + (y - B->lo[1])) * B->bnx + (x - B->lo[0]);
         B->fbox[bi] = ax;
         B->fbox[B->bcells + bi] = ay;
@@ -828,8 +866,8 @@ __device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, 
 // The update of one rotor tile: cull the blade elements whose support reaches
 // the tile into shared memory (in element order; when more than KCULL reach it
 // every cell scans all elements), then each cell as in the bulk path plus the
-// Gaussian-regularised blade force, and in the last rotor tile of its lattice
-// to finish, the actuator line of the next step.  CTA-wide; only the rotor
+// regularised blade force (Gaussian or Roma), and in the last rotor tile of its
+// lattice to finish, the actuator line of the next step.  CTA-wide; only the rotor
 // launch of k_step contains it.  Adds the cells' diagnostic partial sums to
 // sums[4].
 template <int COLL, typename T, bool MARCH, int KCULL>

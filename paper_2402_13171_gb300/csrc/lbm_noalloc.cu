@@ -95,7 +95,11 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
     const int n_el = d->n_blades * d->n_elements;
     if (d->n_blades < 1 || d->n_elements < 1 || n_el > kStaticMaxElements) return LBM_ERR_INVALID_ARG;
     if (d->n_polar < 2 || d->n_polar > kStaticMaxPolar || !d->alpha || !d->cl || !d->cd) return LBM_ERR_INVALID_ARG;
-    if (!(d->epsilon >= 0.5 && d->epsilon <= 5.0) || !(d->radius > 0.0)) return LBM_ERR_INVALID_ARG;
+    if (d->regularisation != ALM_REG_GAUSSIAN && d->regularisation != ALM_REG_ROMA) return LBM_ERR_INVALID_ARG;
+    if (d->tip_loss != 0 && d->tip_loss != 1) return LBM_ERR_INVALID_ARG;
+    const bool roma = d->regularisation == ALM_REG_ROMA;
+    if ((!roma && !(d->epsilon >= 0.5 && d->epsilon <= 5.0)) || !(d->radius > 0.0)) return LBM_ERR_INVALID_ARG;
+    const double cut = roma ? 1.5 : 3.0 * d->epsilon;
     for (int i = 1; i < d->n_polar; ++i)
         if (!(d->alpha[i] > d->alpha[i - 1])) return LBM_ERR_INVALID_ARG;
     const double cy = std::cos(d->yaw), sy = std::sin(d->yaw);
@@ -103,7 +107,7 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
     const int n[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a) {
         // same support rule as alm_add_turbine: the sampled cells stay inside [1, n-2]
-        const double ext = d->radius * std::sqrt(std::max(0.0, 1.0 - ea[a] * ea[a])) + 3.0 * d->epsilon + 1.0;
+        const double ext = d->radius * std::sqrt(std::max(0.0, 1.0 - ea[a] * ea[a])) + cut + 1.0;
         if (std::floor(d->hub[a] - ext) < 1 || std::ceil(d->hub[a] + ext) > n[a] - 2) return LBM_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -124,9 +128,11 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
     B.radius = (float)d->radius;
     B.n_blades = d->n_blades;
     B.n_elements = d->n_elements;
-    B.eps = (float)d->epsilon;
-    B.inv_eps2 = (float)(1.0 / (d->epsilon * d->epsilon));
-    B.cut = (float)(3.0 * d->epsilon);
+    B.eps = roma ? 0.0f : (float)d->epsilon;
+    B.inv_eps2 = roma ? 0.0f : (float)(1.0 / (d->epsilon * d->epsilon));
+    B.cut = (float)cut;
+    B.roma = roma ? 1 : 0;
+    B.tip_loss = d->tip_loss;
     B.omega = d->omega;
     B.theta0 = d->theta0;
     B.pitch = (float)d->pitch;

@@ -62,7 +62,12 @@ class AlmTurbineDesc(ctypes.Structure):
         ("chord_root", ctypes.c_double), ("chord_tip", ctypes.c_double),
         ("twist", _dp), ("n_polar", ctypes.c_int),
         ("alpha", _dp), ("cl", _dp), ("cd", _dp),
+        ("regularisation", ctypes.c_int),
+        ("tip_loss", ctypes.c_int),
     ]
+
+
+REGULARISATION = {"gauss": 0, "roma": 1}
 
 
 class LbmError(RuntimeError):
@@ -93,12 +98,14 @@ def load():
         "lbm_get_pdfs": [ctypes.c_void_p, _dp],
         "lbm_set_pdfs": [ctypes.c_void_p, _dp],
         "alm_get_loads": [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _fp, _fp],
+        "alm_get_loads_async": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
         "lbm_get_diagnostics": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_get_step": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_set_step": [ctypes.c_void_p, ctypes.c_longlong],
         "lbm_set_profiling": [ctypes.c_void_p, ctypes.c_int],
         "lbm_get_kernel_time": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_get_traffic_model": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
+        "lbm_get_launches_per_step": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)],
         "lbm_set_tile": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "lbm_probe": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, _dp, _dp],
         "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
@@ -229,7 +236,10 @@ class Lattice:
         self._call("lbm_init_fields", _p(r), _p(v), _p(g, _fp))
 
     def add_turbine(self, hub, radius, n_blades, n_elements, epsilon, omega, alpha, cl, cd, yaw=0.0, pitch=0.0,
-                    theta0=0.0, chord_root=1.0, chord_tip=1.0, twist=None):
+                    theta0=0.0, chord_root=1.0, chord_tip=1.0, twist=None, kernel="gauss", tip_loss=False):
+        """Add a rotor; `kernel` is the force regularisation, "gauss" (width
+        epsilon) or "roma" (Roma et al.'s three-point delta, epsilon unused);
+        `tip_loss` applies Glauert's tip-loss factor to the element forces."""
         arrs = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in
                 dict(alpha=alpha, cl=cl, cd=cd).items()}
         tw = None if twist is None else np.ascontiguousarray(twist, dtype=np.float64)
@@ -246,6 +256,8 @@ class Lattice:
         d.twist = _p(tw)
         d.n_polar = arrs["alpha"].size
         d.alpha, d.cl, d.cd = _p(arrs["alpha"]), _p(arrs["cl"]), _p(arrs["cd"])
+        d.regularisation = REGULARISATION[kernel] if isinstance(kernel, str) else int(kernel)
+        d.tip_loss = int(tip_loss)
         tid = ctypes.c_int()
         self._call("alm_add_turbine", ctypes.byref(d), ctypes.byref(tid))
         self.turbines.append(int(n_blades) * int(n_elements))
@@ -294,6 +306,18 @@ class Lattice:
             return th.value, tq.value, ef, ep
         return th.value, tq.value
 
+    def loads_async(self, out, tid=0):
+        """Enqueue the copy of the last enqueued step's (thrust, torque) into
+        `out`, a page-locked float64 torch tensor of 2 elements, on the
+        lattice's stream; read it after an event recorded behind it."""
+        assert out.dtype == self._torch().float64 and out.numel() == 2 and out.is_pinned()
+        self._call("alm_get_loads_async", int(tid), ctypes.c_void_p(out.data_ptr()))
+
+    @staticmethod
+    def _torch():
+        import torch
+        return torch
+
     def diagnostics(self):
         out = np.zeros(4)
         at = ctypes.c_longlong()
@@ -337,6 +361,11 @@ class Lattice:
         n = ctypes.c_longlong()
         self._call("lbm_get_traffic_model", ctypes.byref(b), ctypes.byref(n))
         return b.value, n.value
+
+    def launches_per_step(self):
+        n = ctypes.c_int()
+        self._call("lbm_get_launches_per_step", ctypes.byref(n))
+        return n.value
 
     def destroy(self):
         if self._h is not None and self._h.value:

@@ -148,24 +148,27 @@ def test_inlet_outlet_noise():
     assert max_du(g, s) <= DU_TOL
 
 
-def small_rotor_case(collision="cumulant"):
-    dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777)
+def small_rotor_case(collision="cumulant", kernel="gauss", tip_loss=False):
+    dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777, kernel=kernel,
+                                      tip_loss=tip_loss)
     dom["collision"] = collision
     return dom, turb
 
 
-@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
-def test_rotor_short_horizon(coll):
+@pytest.mark.parametrize("coll,kernel,tip_loss", [("cumulant", "gauss", False), ("srt_smag", "gauss", False),
+                                                  ("cumulant", "roma", False), ("cumulant", "gauss", True)])
+def test_rotor_short_horizon(coll, kernel, tip_loss):
     """Actuator line + inlet/outlet + noise on a scaled-down single-rotor case:
-    flow, element forces and FP64 rotor loads stay with the oracle."""
-    dom, turb = small_rotor_case(coll)
+    flow, element forces and FP64 rotor loads stay with the oracle, for both
+    regularisation kernels and with Glauert's tip-loss factor."""
+    dom, turb = small_rotor_case(coll, kernel, tip_loss)
     g, s = setup_pair(dom, [turb], inflow=True)
     for n in (1, 10, 50):
         g.step(n - s.step_count)
         s.step(n - s.step_count)
         du = max_du(g, s)
         th, tq, ef, ep = g.loads(0, elements=True)
-        print(f"{coll} step {n}: max|du| {du:.2e}  thrust {th:.6e} vs {s.loads[0, 0]:.6e}")
+        print(f"{coll}/{kernel}/tip_loss={tip_loss} step {n}: max|du| {du:.2e}  thrust {th:.6e} vs {s.loads[0, 0]:.6e}")
         assert du <= DU_TOL
         np.testing.assert_allclose(ep, s.elem_pos, atol=2e-5)
         # element forces scale with |u_rel|^2: relative error ~ 2 max|du| / |u_rel| <= 2e-6 / 0.05
@@ -174,14 +177,15 @@ def test_rotor_short_horizon(coll):
         assert tq == pytest.approx(s.loads[0, 1], rel=5e-5)
 
 
-def test_rotor_force_sum_matches_blade_forces():
+@pytest.mark.parametrize("kernel", ["gauss", "roma"])
+def test_rotor_force_sum_matches_blade_forces(kernel):
     """One step of momentum change equals minus the applied blade forces.
 
     The background is a uniform flow, whose cells all round alike in FP32; the
     same lattice without the rotor is stepped beside it, so that every cell
     outside the force support (bitwise the same in both) cancels and only the
     spread force remains."""
-    dom, turb = small_rotor_case()
+    dom, turb = small_rotor_case(kernel=kernel)
     dom["bc"] = ("periodic", "periodic", "periodic")
     u0 = np.stack([np.full((40, 40, 64), 0.05), np.zeros((40, 40, 64)), np.zeros((40, 40, 64))])
     g, s = setup_pair(dom, [turb], u=u0)
@@ -199,12 +203,13 @@ def test_rotor_force_sum_matches_blade_forces():
     g_free.destroy()
 
 
-def test_full_size_single_turbine_sampled():
+@pytest.mark.parametrize("kernel", ["gauss", "roma"])
+def test_full_size_single_turbine_sampled(kernel):
     """256x128x128 single-rotor workload in the launch configuration of the
     benchmark: one step from a seeded state, checked at sampled cells (rotor
     box, inlet, outlet, bulk) and on every element force, against the
     oracle's per-cell update."""
-    dom, turb = I.single_turbine_case()
+    dom, turb = I.single_turbine_case(kernel=kernel)
     nx, ny, nz = dom["nx"], dom["ny"], dom["nz"]
     rho, u, fneq = I.random_state(nx, ny, nz, seed=4242, u_mean=(0.05, 0, 0), du=0.005, drho=0.002, fneq_amp=2e-4)
     g, s = setup_pair(dom, [turb], rho=rho, u=u, fneq=fneq, inflow=True)
@@ -221,9 +226,11 @@ def test_full_size_single_turbine_sampled():
     cells = [(0, 5, 7), (255, 127, 0), (64, 64, 64), (60, 50, 70), (70, 80, 48), (1, 0, 127), (254, 64, 3)]
     cells += [tuple(int(v) for v in c) for c in rng.integers([52, 42, 42], [76, 86, 86], (12, 3))]
     cells += [tuple(int(v) for v in c) for c in rng.integers([0, 0, 0], [256, 128, 128], (12, 3))]
+    # cells nearest to every tenth element: inside even the 3-cell Roma support
+    cells += [tuple(int(v) for v in np.round(p)) for p in pos[::10]]
     eps = turb["epsilon"]
     for (x, y, z) in cells:
-        F = O.spread_at(pos, fb, eps, x, y, z)
+        F = O.spread_at(pos, fb, eps, x, y, z, kernel=kernel)
         ref = s.update_cell(f0, F, 0, x, y, z)
         np.testing.assert_allclose(fg[:, z, y, x], ref, atol=F_TOL, rtol=0, err_msg=str((x, y, z)))
 
@@ -317,6 +324,33 @@ def test_graph_replay_equals_direct_launches():
     np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
     ms, n = gb.kernel_time()
     assert n == 9 and ms > 0
+    # a step is the rotor-tile launch plus the rest; without a rotor, one launch
+    assert gb.launches_per_step() == 2
+    g0 = gpu_lattice(dom)
+    assert g0.launches_per_step() == 1
+    g0.destroy()
+
+
+def test_async_loads_match_synchronous_reads():
+    """alm_get_loads_async enqueued after each of six steps, with no wait in
+    between, gives every step's thrust and torque as the synchronising read
+    does on an identical lattice."""
+    import torch
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    gs, _ = setup_pair(dom, [turb], inflow=True)
+    buf = torch.zeros((6, 2), dtype=torch.float64).pin_memory()
+    ref = []
+    for i in range(6):
+        ga.step(1)
+        ga.loads_async(buf[i])
+        gs.step(1)
+        ref.append(gs.loads(0))
+    ga.sync()
+    np.testing.assert_array_equal(buf.numpy(), np.array(ref))
+    assert np.all(buf.numpy()[:, 0] > 0)
+    ga.destroy()
+    gs.destroy()
 
 
 def test_checkpoint_resume_is_bitwise():

@@ -1,6 +1,7 @@
 """Host-side argument checks of the C ABI, which run before any CUDA call:
 lattice sizes (including the 32-bit plane-offset limit 27 N < 2^31), boundary
-codes, viscosity, tiles, and batches whose members disagree."""
+codes, viscosity, tiles, batches whose members disagree, and the rotor of the
+allocation-free actuator-line entry point."""
 import ctypes
 
 import pytest
@@ -55,3 +56,45 @@ def test_status_strings_cover_every_code():
     L = lbm.load()
     for code in range(8):
         assert L.lbm_status_string(code)
+
+
+def _static_desc(**over):
+    import numpy as np
+    from paper_2402_13171_gb300 import inputs as I
+    t = I.single_turbine(64, 40, 40, diameter=16.0, elements_per_blade=8)
+    keep = [np.ascontiguousarray(t[k], dtype=np.float64) for k in ("alpha", "cl", "cd")]
+    d = lbm.AlmTurbineDesc()
+    for a in range(3):
+        d.hub[a] = t["hub"][a]
+    d.radius, d.n_blades, d.n_elements = t["radius"], t["n_blades"], t["n_elements"]
+    d.epsilon, d.omega = t["epsilon"], t["omega"]
+    d.chord_root, d.chord_tip = t["chord_root"], t["chord_tip"]
+    d.n_polar = keep[0].size
+    d.alpha, d.cl, d.cd = (k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k in keep)
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d, keep
+
+
+@pytest.mark.parametrize("over", [dict(regularisation=2), dict(regularisation=-1),
+                                  dict(tip_loss=2), dict(tip_loss=-1),
+                                  dict(epsilon=0.0), dict(epsilon=6.0), dict(radius=0.0),
+                                  dict(hub=(16.0, 10.9, 20.0), regularisation=1)])
+def test_static_alm_rejects_bad_rotors_on_the_host(over):
+    """alm_eval_static checks its rotor before any CUDA call: an unknown
+    regularisation or tip-loss code, a Gaussian width outside [0.5, 5], a zero radius, or
+    a Roma support (hub +- (R + 3/2 + 1)) that leaves [1, n-2]."""
+    L = lbm.load()
+    fn = L.alm_eval_static
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                   ctypes.POINTER(lbm.AlmTurbineDesc), ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_void_p]
+    hub = over.pop("hub", None)
+    d, keep = _static_desc(**over)
+    if hub is not None:
+        for a in range(3):
+            d.hub[a] = hub[a]
+    # the PDF, force and load pointers are only tested for NULL before the checks fail
+    dummy = ctypes.c_void_p(256)
+    assert fn(dummy, 64, 40, 40, None, ctypes.byref(d), 0, dummy, None, dummy, None) == INVALID_ARG
