@@ -63,6 +63,7 @@ struct Batch {
     long long prof_n = 0;
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [long?][start parity]
     unsigned n_rotor = 0;                 // rotor tiles at the head of the work list
+    int rotor_planes = 1;                 // planes of the deepest rotor tile
     long long* d_probe = nullptr;   // probe cell list and results, grown on demand
     double* d_probe_out = nullptr;
     int probe_cap = 0;
@@ -252,24 +253,55 @@ lbm_status sync_descriptors(Batch* b)
 {
     if (!b->dirty) return LBM_OK;
     std::vector<unsigned long long> rotor, rest;
+    // rotor tiles: the z-blocks of a column that reach a rotor box, runs of them
+    // merged up to kRotorPlanes planes (not for the staged kernel's row segments)
+    const int merge = b->staged ? 1 : std::max(1, kRotorPlanes / b->tile_z);
+    int rotor_planes = 1;
     for (size_t i = 0; i < b->inst.size(); ++i) {
         Instance& I = b->inst[i];
-        int nrot = 0;
-        for (int z = 0; z < I.h.nz; z += b->tile_z)
-            for (int y0 = 0; y0 < I.h.ny; y0 += b->tile_y)
-                for (int x0 = 0; x0 < I.h.nx; x0 += b->tile_x) {
-                    bool hit = false;
+        const int nzb = (I.h.nz + b->tile_z - 1) / b->tile_z;
+        const int nyb = (I.h.ny + b->tile_y - 1) / b->tile_y, nxb = (I.h.nx + b->tile_x - 1) / b->tile_x;
+        // planes[(k * nyb + j) * nxb + l]: 0 for a bulk tile, -1 for a z-block inside a
+        // merged rotor tile that starts below it, else the rotor tile's planes
+        std::vector<int> planes((size_t)nzb * nyb * nxb, 0);
+        for (int j = 0; j < nyb; ++j)
+            for (int l = 0; l < nxb; ++l) {
+                const int y0 = j * b->tile_y, x0 = l * b->tile_x;
+                auto hit = [&](int k) {
+                    const int z = k * b->tile_z;
                     for (auto& t : I.turb) {
                         const DevTurbine& B = t.dev;
                         if (z <= B.hi[2] && z + b->tile_z - 1 >= B.lo[2] && y0 <= B.hi[1] &&
                             y0 + b->tile_y - 1 >= B.lo[1] && x0 <= B.hi[0] && x0 + b->tile_x - 1 >= B.lo[0])
-                            hit = true;
+                            return true;
                     }
-                    if (hit) {
-                        rotor.push_back(pack_tile((int)i, z, y0, x0, true));
-                        ++nrot;
-                    } else {
+                    return false;
+                };
+                for (int k = 0; k < nzb;) {
+                    if (!hit(k)) {
+                        ++k;
+                        continue;
+                    }
+                    int run = 1;
+                    while (run < merge && k + run < nzb && hit(k + run)) ++run;
+                    planes[((size_t)k * nyb + j) * nxb + l] = std::min(run * b->tile_z, I.h.nz - k * b->tile_z);
+                    for (int r = 1; r < run; ++r) planes[((size_t)(k + r) * nyb + j) * nxb + l] = -1;
+                    k += run;
+                }
+            }
+        // z-major order (x fastest), as the bulk streams plane after plane
+        int nrot = 0;
+        for (int k = 0; k < nzb; ++k)
+            for (int j = 0; j < nyb; ++j)
+                for (int l = 0; l < nxb; ++l) {
+                    const int p = planes[((size_t)k * nyb + j) * nxb + l];
+                    const int z = k * b->tile_z, y0 = j * b->tile_y, x0 = l * b->tile_x;
+                    if (p == 0) {
                         rest.push_back(pack_tile((int)i, z, y0, x0, false));
+                    } else if (p > 0) {
+                        rotor.push_back(pack_tile((int)i, z, y0, x0, true, p));
+                        rotor_planes = std::max(rotor_planes, p);
+                        ++nrot;
                     }
                 }
         I.h.n_rotor_tiles = nrot;
@@ -289,6 +321,7 @@ lbm_status sync_descriptors(Batch* b)
     }
     b->n_tiles = (unsigned)tiles.size();
     b->n_rotor = (unsigned)rotor.size();
+    b->rotor_planes = rotor_planes;
     CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(unsigned long long) * tiles.size(), cudaMemcpyHostToDevice,
                        b->stream));
     std::vector<DevDomain> doms;
@@ -349,6 +382,7 @@ lbm_status launch_one(Batch* b, int parity)
     StepArgs ar = a, ab = a;
     ar.n_tiles = R;
     ar.write_step = Nb == 0 ? 1 : 0;
+    ar.tile_z = b->rotor_planes;  // > 1: the marching rotor kernel, each tile over its own planes
     ab.tiles = b->d_tiles + R;
     ab.n_tiles = Nb;
     if (R > 0) CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));

@@ -92,17 +92,25 @@ struct StepArgs {
     int* diag_flag;                     // slot [parity]: 1 if step n is a diagnostic step; CTA 0 writes n+1's
     unsigned int* diag_done;            // CTA completion counter, used on diagnostic steps only
     int diag_every;                     // diagnostic period shared by the batch (0 = off)
-    int tile_z;                         // planes per CTA (1: no marching)
+    int tile_z;                         // planes per CTA (1: no marching); for the rotor launch the deepest rotor tile
     int staged;                         // rows staged in shared memory by persistent CTAs
 };
 
-// Work-list entry: bit 63 rotor tile, bits 48..62 instance, 32..47 z, 16..31 y0, 0..15 x0.
-__host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0, int x0, bool rotor)
+// Planes a rotor tile covers at most (consecutive z-blocks of its column are
+// merged up to this depth), so that one CTA culls the blade elements once for
+// several planes and the rotor launch stays within one wave.
+constexpr int kRotorPlanes = 4;
+
+// Work-list entry: bit 63 rotor tile, bits 56..62 planes - 1 (rotor tiles),
+// 48..55 lattice, 32..47 z, 16..31 y0, 0..15 x0.
+__host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0, int x0, bool rotor, int planes = 1)
 {
-    return ((unsigned long long)(rotor ? 1u : 0u) << 63) | ((unsigned long long)(inst & 0x7FFF) << 48) |
-           ((unsigned long long)(z & 0xFFFF) << 32) | ((unsigned long long)(y0 & 0xFFFF) << 16) |
-           (unsigned long long)(x0 & 0xFFFF);
+    return ((unsigned long long)(rotor ? 1u : 0u) << 63) | ((unsigned long long)((planes - 1) & 0x7F) << 56) |
+           ((unsigned long long)(inst & 0xFF) << 48) | ((unsigned long long)(z & 0xFFFF) << 32) |
+           ((unsigned long long)(y0 & 0xFFFF) << 16) | (unsigned long long)(x0 & 0xFFFF);
 }
+__host__ __device__ inline int tile_lattice(unsigned long long t) { return (int)((t >> 48) & 0xFF); }
+__host__ __device__ inline int tile_planes(unsigned long long t) { return (int)((t >> 56) & 0x7F) + 1; }
 
 // Host-side launchers (lbm_kernels.cu).
 // rotor: the launch over the rotor tiles (element culling, force gather, the

@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 namespace lbmgb {
 
 // ------------------------------------------------------------------ lattice
@@ -868,12 +870,12 @@ __device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, 
 // every cell scans all elements), then each cell as in the bulk path plus the
 // regularised blade force (Gaussian or Roma), and in the last rotor tile of its
 // lattice to finish, the actuator line of the next step.  CTA-wide; only the rotor
-// launch of k_step contains it.  Adds the cells' diagnostic partial sums to
-// sums[4].
+// launch of k_step contains it.  Writes the thread's diagnostic partial sums
+// (zero unless diag) to sums[4].
 template <int COLL, typename T, bool MARCH, int KCULL>
 __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned long long tile, long long step, int parity,
-                                               int tile_z, float4* s_pos, float4* s_frc, int* s_tag, int* s_cnt,
-                                               int* s_flag, float* sums)
+                                               int planes, bool diag, float4* s_pos, float4* s_frc, int* s_tag,
+                                               int* s_cnt, int* s_flag, double* sums)
 {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
@@ -881,7 +883,7 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
     const int nx = D->nx, ny = D->ny, nz = D->nz;
-    const int z1 = MARCH ? min(z0 + tile_z, nz) : z0 + 1;  // planes [z0, z1)
+    const int z1 = MARCH ? min(z0 + planes, nz) : z0 + 1;  // planes [z0, z1)
     const unsigned uN = (unsigned)D->N;
     const T* __restrict__ src = (const T*)D->f[parity];
     T* __restrict__ dst = (T*)D->f[parity ^ 1];
@@ -927,7 +929,10 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
         n_cull = total <= KCULL ? total : -1;
     }
 
-    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    // diagnostic partial sums of the thread's planes (diagnostic steps only),
+    // in FP64 when it marches over several planes
+    using Acc = typename std::conditional<MARCH, double, float>::type;
+    Acc o_m = 0, o_jx = 0, o_jy = 0, o_jz = 0;
     if (x < nx && y < ny) {
         float hn[27];
         load_cell<T>(D, src, x, y, z0, step, hn);
@@ -953,19 +958,21 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
                 collide_cumulant(h, F[0], F[1], F[2], D->omega, m, jx, jy, jz);
             else
                 collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, m, jx, jy, jz);
-            o_m += m;
-            o_jx += jx;
-            o_jy += jy;
-            o_jz += jz;
+            if (diag) {
+                o_m += m;
+                o_jx += jx;
+                o_jy += jy;
+                o_jz += jz;
+            }
             const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
 #pragma unroll
             for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
         }
     }
-    sums[0] += o_m;
-    sums[1] += o_jx;
-    sums[2] += o_jy;
-    sums[3] += o_jz;
+    sums[0] = (double)o_m;
+    sums[1] = (double)o_jx;
+    sums[2] = (double)o_jy;
+    sums[3] = (double)o_jz;
 
     // last rotor tile of this lattice: actuator line of the next step
     __syncthreads();
@@ -1003,7 +1010,7 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
     __shared__ int s_tag[kCull];
     __shared__ int s_cnt[8];
     const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
-    const int inst = (int)((tile >> 48) & 0x7FFF);
+    const int inst = tile_lattice(tile);
     const int z0 = (int)((tile >> 32) & 0xFFFF);
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
@@ -1014,14 +1021,17 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
         A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
     }
     const bool diag = __ldcg(A.diag_flag + A.parity) != 0;  // uniform over the grid
-    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    // diagnostic partial sums of the thread's planes (diagnostic steps only),
+    // in FP64 when it marches over several planes
+    using Acc = typename std::conditional<MARCH, double, float>::type;
+    Acc o_m = 0, o_jx = 0, o_jy = 0, o_jz = 0;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
 
     if constexpr (ROTOR) {
-        float sums[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        rotor_tile_update<COLL, T, MARCH, kCull>(D, tile, step, A.parity, A.tile_z, s_pos, s_frc, s_tag, s_cnt,
-                                                 &s_flag, sums);
+        double sums[4];
+        rotor_tile_update<COLL, T, MARCH, kCull>(D, tile, step, A.parity, tile_planes(tile), diag, s_pos, s_frc,
+                                                 s_tag, s_cnt, &s_flag, sums);
         o_m = sums[0];
         o_jx = sums[1];
         o_jy = sums[2];
@@ -1056,10 +1066,12 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
                     collide_cumulant(h, D->body[0], D->body[1], D->body[2], D->omega, m, jx, jy, jz);
                 else
                     collide_srt_smag(h, D->body[0], D->body[1], D->body[2], D->tau0, D->smag_c2, m, jx, jy, jz);
-                o_m += m;
-                o_jx += jx;
-                o_jy += jy;
-                o_jz += jz;
+                if (diag) {
+                    o_m += m;
+                    o_jx += jx;
+                    o_jy += jy;
+                    o_jz += jz;
+                }
                 const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
 #pragma unroll
                 for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
@@ -1175,7 +1187,7 @@ __device__ __forceinline__ void bulk_issue(const StepArgs& A, unsigned it, T* st
     constexpr int H = halo_of<T>();
     const int lane = threadIdx.x & 31;
     const unsigned long long tile = A.tiles[it];
-    const DevDomain* D = A.dom + ((tile >> 48) & 0x7FFF);
+    const DevDomain* D = A.dom + tile_lattice(tile);
     const int z = (int)((tile >> 32) & 0xFFFF), y = (int)((tile >> 16) & 0xFFFF), x0 = (int)(tile & 0xFFFF);
     const int nx = D->nx, ny = D->ny, nz = D->nz;
     const int lo = max(x0 - H, 0), hi = min(x0 + W + H, nx);
@@ -1269,7 +1281,7 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
 
         const unsigned long long tile = A.tiles[it];
         const bool rotor_tile = (tile >> 63) != 0;
-        const DevDomain* D = A.dom + ((tile >> 48) & 0x7FFF);
+        const DevDomain* D = A.dom + tile_lattice(tile);
         const int z = (int)((tile >> 32) & 0xFFFF);
         const int y = (int)((tile >> 16) & 0xFFFF);
         const int x0 = (int)(tile & 0xFFFF);
