@@ -44,8 +44,8 @@ def parse_args():
                    help="CTA tile XxY, XxYxZ or XxYxZxS (S = 1: rows staged in shared memory), or 'auto' "
                         "(the library's autotuner, cached)")
     p.add_argument("--workload", choices=["single", "batch16", "precision", "warmstart", "tilesweep"], default="single",
-                   help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices in one launch per "
-                        "step; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles; "
+                   help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices stepped by "
+                        "the same two launches; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles; "
                         "warmstart: 3x3 farm, steps to a settled mean from a cold vs a surrogate warm start; "
                         "tilesweep: the single-rotor workload at every tile candidate of the tuner")
     p.add_argument("--no-cpu-baseline", action="store_true")
