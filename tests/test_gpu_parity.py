@@ -235,14 +235,18 @@ def test_full_size_single_turbine_sampled(kernel):
         np.testing.assert_allclose(fg[:, z, y, x], ref, atol=F_TOL, rtol=0, err_msg=str((x, y, z)))
 
 
-@pytest.mark.parametrize("tile", [(128, 1), (64, 2), (256, 1), (96, 1), (32, 8), (32, 4, 4), (32, 2, 7), (64, 2, 64)])
+@pytest.mark.parametrize("tile", [(128, 1), (64, 2), (256, 1), (96, 1), (32, 8), (32, 4, 4), (32, 2, 7), (64, 2, 64),
+                                  (32, 4, 2), (64, 1, 2)])
 def test_tile_shapes_agree(tile):
+    """Every CTA shape and marching depth, with rotor tiles merged over 1-4
+    planes (2-plane z-blocks merge in pairs), steps bitwise like the default."""
     dom, turb = small_rotor_case()
     ga, _ = setup_pair(dom, [turb], inflow=True)
     gb, _ = setup_pair(dom, [turb], inflow=True, tile=tile)
     ga.step(7)
     gb.step(7)
     np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    assert ga.loads(0) == gb.loads(0)
 
 
 @pytest.mark.parametrize("bc", [("periodic", "periodic", "periodic"), ("inout", "periodic", "freeslip"),
