@@ -999,8 +999,12 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
 // evaluated by the last rotor CTA, runs under the bulk.  The two launches
 // write disjoint cells.  The bulk launch's last CTA waits for the rotor launch
 // before it exits, so the bulk launch ends only after both.
+// Register budgets (blocks of up to 256 threads): 64 per thread for the
+// single-plane cumulant bulk, whose collision fits them without spills, so 8
+// CTAs of 128 threads (32 warps) are resident per SM; 85 for the rotor tiles
+// and the Smagorinsky collision; 128 for marching, which holds two planes.
 template <int COLL, typename T, bool MARCH, bool ROTOR>
-__global__ void __launch_bounds__(256, MARCH ? 2 : 3) k_step(const StepArgs A)
+__global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMULANT) ? 3 : 4)) k_step(const StepArgs A)
 {
     if (ROTOR) asm volatile("griddepcontrol.launch_dependents;");
     constexpr int kCull = 128;  // blade elements kept per rotor tile

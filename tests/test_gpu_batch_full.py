@@ -1,8 +1,9 @@
 """The batched sweep at full size (16 seeded single-rotor lattices, 71.9 M
-cells) in the launch configuration the benchmark times (tile 32x4x8, z-marching,
-rotor tiles of 8 planes): one batched step from seeded near-equilibrium states,
-checked against the FP64 oracle lattice by lattice on every element force and
-rotor load and on sampled cells (next to blade elements, inlet, outlet, bulk).
+cells) in the launch configurations the benchmark's tuner picks (32x4x1 with
+rotor tiles of 4 planes; 32x4x8, z-marching): one batched step from seeded
+near-equilibrium states, checked against the FP64 oracle lattice by lattice on
+every element force and rotor load and on sampled cells (next to blade
+elements, inlet, outlet, bulk).
 
 Tolerances as in the single-lattice full-size test: element positions 2e-5,
 element forces 1e-5 of the largest, loads 1e-5 relative, PDFs 2e-7 absolute.
@@ -31,11 +32,12 @@ def _state(i, dom):
                           du=0.005, drho=0.002, fneq_amp=2e-4)
 
 
-def test_full_size_batch16_sampled():
+@pytest.mark.parametrize("tile", [(32, 4, 1), (32, 4, 8)])
+def test_full_size_batch16_sampled(tile):
     from paper_2402_13171_gb300 import lbm
     cases = I.batch_instances(16)
     cfgs = [dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], collision=d["collision"], nu=d["nu"], smag_c=d["smag_c"],
-                 bc=d["bc"], seed=d["seed"], tile=(32, 4, 8)) for d, _ in cases]
+                 bc=d["bc"], seed=d["seed"], tile=tile) for d, _ in cases]
     lat = lbm.batch_create(cfgs)
     assert sum(L.N for L in lat) == 71866368
     before = []
@@ -45,7 +47,7 @@ def test_full_size_batch16_sampled():
         rho, u, fneq = _state(i, d)
         L.init_fields(rho, u, fneq)
         before.append(L.loads(0, elements=True))
-    assert lat[0].tile()[:3] == (32, 4, 8)
+    assert lat[0].tile()[:3] == tile
     lat[0].step(1)
     rng = np.random.default_rng(77)
     for i, (L, (d, t)) in enumerate(zip(lat, cases)):

@@ -203,16 +203,17 @@ def test_rotor_force_sum_matches_blade_forces(kernel):
     g_free.destroy()
 
 
-@pytest.mark.parametrize("kernel", ["gauss", "roma"])
-def test_full_size_single_turbine_sampled(kernel):
-    """256x128x128 single-rotor workload in the launch configuration of the
-    benchmark: one step from a seeded state, checked at sampled cells (rotor
-    box, inlet, outlet, bulk) and on every element force, against the
-    oracle's per-cell update."""
+@pytest.mark.parametrize("kernel,tile", [("gauss", (32, 4, 1)), ("roma", (32, 4, 1)), ("gauss", (32, 8, 1))])
+def test_full_size_single_turbine_sampled(kernel, tile):
+    """256x128x128 single-rotor workload in the launch configurations the
+    benchmark's tuner picks (32x4x1, 32x8x1): one step from a seeded state,
+    checked at sampled cells (rotor box, inlet, outlet, bulk) and on every
+    element force, against the oracle's per-cell update."""
     dom, turb = I.single_turbine_case(kernel=kernel)
     nx, ny, nz = dom["nx"], dom["ny"], dom["nz"]
     rho, u, fneq = I.random_state(nx, ny, nz, seed=4242, u_mean=(0.05, 0, 0), du=0.005, drho=0.002, fneq_amp=2e-4)
-    g, s = setup_pair(dom, [turb], rho=rho, u=u, fneq=fneq, inflow=True)
+    g, s = setup_pair(dom, [turb], rho=rho, u=u, fneq=fneq, inflow=True, tile=tile)
+    assert g.tile()[:3] == tile
     f0 = s.f.copy()
     # oracle: element forces of step 0 and the spread force at sampled cells
     pos, fb, alpha, loads = s.alm_forces(f0, np.zeros((3, nz, ny, nx)), 0)

@@ -40,10 +40,13 @@ def _desc(t):
     d.alpha = keep["alpha"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     d.cl = keep["cl"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     d.cd = keep["cd"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.regularisation = lbm.REGULARISATION[t["kernel"]]
+    d.tip_loss = int(t["tip_loss"])
     return d, keep
 
 
-def test_static_alm_matches_lattice_on_two_calls():
+@pytest.mark.parametrize("kernel,tip_loss", [("gauss", False), ("roma", True)])
+def test_static_alm_matches_lattice_on_two_calls(kernel, tip_loss):
     import torch
     from paper_2402_13171_gb300 import build
     build.build()
@@ -54,7 +57,8 @@ def test_static_alm_matches_lattice_on_two_calls():
                    ctypes.POINTER(lbm.AlmTurbineDesc), ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
                    ctypes.c_void_p, ctypes.c_void_p]
     nx, ny, nz = 64, 40, 40
-    dom, turb = I.single_turbine_case(nx, ny, nz, diameter=16.0, elements_per_blade=8, seed=31)
+    dom, turb = I.single_turbine_case(nx, ny, nz, diameter=16.0, elements_per_blade=8, seed=31, kernel=kernel,
+                                      tip_loss=tip_loss)
     body = (2e-6, 0.0, -1e-6)
     g = lbm.Lattice.create(nx, ny, nz, nu=dom["nu"], bc=("periodic",) * 3, body_force=body)
     g.add_turbine(**turb)
