@@ -33,6 +33,11 @@
  *    caller owns every host array it passes; tables are copied.
  *  - Calls that return host data synchronise the context's stream; lbm_step
  *    only enqueues work.
+ *  - Fault injection for tests, on the host only: the environment variable
+ *    LBM_FAULT=alloc fails every device allocation (LBM_ERR_OOM), =capture
+ *    every CUDA graph capture (LBM_ERR_CUDA), =step:N the lbm_step call that
+ *    would run step N (LBM_ERR_CUDA, before it enqueues anything).  It is
+ *    read at each check.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H

@@ -5,9 +5,12 @@
 #include "lbm_gb300.h"
 #include "lbm_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -96,9 +99,29 @@ lbm_status fail(Batch* b, lbm_status s, const std::string& msg, bool sticky = tr
         if (e_ != cudaSuccess) return fail(b, LBM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// NVTX range over a host call, for timeline profilers (free when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Host-side fault injection for tests of the error paths; nothing reaches the
+// GPU.  LBM_FAULT=alloc fails every device allocation, =capture every graph
+// capture, =step:N the lbm_step call that would run step N.  Read at each
+// check, so a process can set and clear it between calls.
+const char* injected_fault(const char* what)
+{
+    const char* f = std::getenv("LBM_FAULT");
+    if (!f) return nullptr;
+    const size_t n = std::strlen(what);
+    if (std::strncmp(f, what, n) != 0 || (f[n] != '\0' && f[n] != ':')) return nullptr;
+    return f + n;
+}
+
 void* dalloc(Batch* b, size_t bytes)
 {
     void* p = nullptr;
+    if (injected_fault("alloc")) return nullptr;
     if (bytes == 0) bytes = 16;
     if (b->ualloc) {
         p = b->ualloc(bytes, b->user);
@@ -570,6 +593,7 @@ lbm_status lbm_set_inflow(lbm_ctx* ctx, const lbm_inflow* in)
 
 lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, const float* fneq)
 {
+    NvtxRange nvtx_("lbm_init_fields");
     ENTER(ctx);
     const long long N = I.h.N;
     lbm_status s = sync_descriptors(b);
@@ -724,6 +748,7 @@ constexpr int kGraphSteps[2] = {2, 8};
 lbm_status ensure_graph(Batch* b, int len, int p)
 {
     if (b->gexec[len][p]) return LBM_OK;
+    if (injected_fault("capture")) return fail(b, LBM_ERR_CUDA, "graph capture failed (injected: LBM_FAULT=capture)");
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     lbm_status s = LBM_OK;
@@ -739,8 +764,14 @@ lbm_status ensure_graph(Batch* b, int len, int p)
 
 lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
 {
+    NvtxRange nvtx_("lbm_step");
     ENTER(ctx);
     if (n_steps < 0) return fail(b, LBM_ERR_INVALID_ARG, "n_steps < 0", false);
+    if (const char* f = injected_fault("step")) {
+        const long long at = *f == ':' ? std::atoll(f + 1) : 0;
+        if (b->host_step <= at && at < b->host_step + n_steps)
+            return fail(b, LBM_ERR_CUDA, "step " + std::to_string(at) + " failed (injected: LBM_FAULT=step:N)");
+    }
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
     int left = n_steps;
@@ -810,6 +841,7 @@ lbm_status lbm_sync(lbm_ctx* ctx)
 
 lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u)
 {
+    NvtxRange nvtx_("lbm_get_moments");
     ENTER(ctx);
     if (!rho || !u) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
     lbm_status s = sync_descriptors(b);
@@ -864,6 +896,7 @@ lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, d
 
 lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f)
 {
+    NvtxRange nvtx_("lbm_get_pdfs");
     ENTER(ctx);
     if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
     const long long N = I.h.N;
@@ -891,6 +924,7 @@ lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f)
 
 lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f)
 {
+    NvtxRange nvtx_("lbm_set_pdfs");
     ENTER(ctx);
     if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null input", false);
     const long long N = I.h.N;
@@ -1111,6 +1145,7 @@ std::string tune_key(Batch* b)
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache_path, int tile_out[4],
                         double* best_ms)
 {
+    NvtxRange nvtx_("lbm_autotune");
     ENTER(ctx);
     if (steps_per_candidate < 1) return fail(b, LBM_ERR_INVALID_ARG, "steps_per_candidate < 1", false);
     const std::string key = tune_key(b);
