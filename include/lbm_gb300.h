@@ -207,6 +207,19 @@ lbm_status alm_get_loads(lbm_ctx* ctx, int id, double* thrust, double* torque, f
  * INVALID_ARG for a bad rotor id or a null output. */
 lbm_status alm_get_loads_async(lbm_ctx* ctx, int id, double* thrust_torque);
 
+/* Zero-copy loads: from the next launch on, the actuator-line evaluation of
+ * step s also writes (thrust, torque) of every rotor t of this lattice into
+ * host_ring[2 ((s mod ring_len) n_turb + t) + {0, 1}].  host_ring must be
+ * page-locked host memory mapped into the device address space (cudaHostAlloc,
+ * or a pinned torch tensor), of 2 n_turb ring_len doubles, owned by the caller
+ * and valid until the sink is cleared (host_ring NULL or ring_len 0) or the
+ * context is destroyed.  The loads of step s are evaluated during step s - 1,
+ * so they are complete once that step's work has finished on the stream (an
+ * event recorded behind it); ring_len >= 3 leaves a step's entry untouched
+ * while the next two steps run.  Adding a rotor clears the sink.
+ * Synchronises.  Errors: INVALID_ARG when host_ring is not mapped. */
+lbm_status alm_set_loads_sink(lbm_ctx* ctx, double* host_ring, int ring_len);
+
 /* FP64 sums [mass, momentum x, y, z] of the last diagnostic step (post-
  * collision state).  Synchronises; NUMERIC if NaN/Inf was seen. */
 lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_step);

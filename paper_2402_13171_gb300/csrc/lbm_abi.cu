@@ -715,6 +715,8 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     B.fbox = d_fbox;
     I.turb.push_back(std::move(t));
     I.h.n_turb = (int)I.turb.size();
+    I.h.loads_sink = nullptr;  // a loads sink is sized for the rotors it was set with
+    I.h.sink_len = 0;
     I.h.n_el += d->n_blades * d->n_elements;
     if (id_out) *id_out = (int)I.turb.size() - 1;
     b->dirty = true;
@@ -992,6 +994,27 @@ lbm_status alm_get_loads_async(lbm_ctx* ctx, int id, double* thrust_torque)
     const int par = b->host_step > 0 ? (int)((b->host_step - 1) & 1) : 0;
     CK(cudaMemcpyAsync(thrust_torque, I.h.loads[par] + 2 * id, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                        b->stream));
+    return LBM_OK;
+}
+
+lbm_status alm_set_loads_sink(lbm_ctx* ctx, double* host_ring, int ring_len)
+{
+    ENTER(ctx);
+    if (!host_ring || ring_len <= 0) {
+        I.h.loads_sink = nullptr;
+        I.h.sink_len = 0;
+    } else {
+        void* dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, host_ring, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(b, LBM_ERR_INVALID_ARG, "loads sink is not mapped page-locked host memory", false);
+        }
+        I.h.loads_sink = (double*)dp;
+        I.h.sink_len = ring_len;
+    }
+    // the descriptor is read by the kernels: upload it before the next launch
+    CK(cudaMemcpyAsync(b->d_dom + ctx->idx, &I.h, sizeof(DevDomain), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     return LBM_OK;
 }
 

@@ -70,6 +70,8 @@ struct DevDomain {
     double* el_load;           // scratch, 2 doubles per element
     float4* el_corner;         // scratch, 8 corners x (rho, u) per element
     double* loads[2];          // by step parity: thrust, torque per rotor
+    double* loads_sink;        // mapped page-locked host ring, or nullptr: step s's loads at [(s % sink_len) n_turb + t] * 2
+    int sink_len;
     int n_el;
     unsigned int* rotor_counter;
     int n_rotor_tiles;

@@ -596,7 +596,8 @@ __device__ __forceinline__ float tip_loss_factor(int n_blades, float R, float r,
 //  phase 2, one thread per element: trilinear blend, relative velocity,
 //    angle of attack, polars, blade force (with the tip-loss factor if set),
 //    kernel normalisation, FP64 loads;
-//  phase 3, warp 0: per-rotor FP64 sums in a fixed order.
+//  phase 3, warp 0: per-rotor FP64 sums in a fixed order (also written to the
+//    host loads sink when one is set).
 template <typename T>
 __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long long step)
 {
@@ -726,6 +727,11 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
             if (tid == 0) {
                 D->loads[par][2 * t] = th;
                 D->loads[par][2 * t + 1] = tq;
+                if (D->loads_sink) {  // zero-copy to the caller's host ring
+                    double* o = D->loads_sink + 2 * ((step % D->sink_len) * D->n_turb + t);
+                    o[0] = th;
+                    o[1] = tq;
+                }
             }
         }
     }

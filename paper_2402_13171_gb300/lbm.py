@@ -99,6 +99,7 @@ def load():
         "lbm_set_pdfs": [ctypes.c_void_p, _dp],
         "alm_get_loads": [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _fp, _fp],
         "alm_get_loads_async": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+        "alm_set_loads_sink": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
         "lbm_get_diagnostics": [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_get_step": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
         "lbm_set_step": [ctypes.c_void_p, ctypes.c_longlong],
@@ -185,6 +186,7 @@ class Lattice:
         self._keep = keep  # allocator callbacks / stream shared by a batch
         self.storage = storage
         self.turbines = []
+        self._sink = None
 
     # -------------------------------------------------------------- creation
     @staticmethod
@@ -261,6 +263,7 @@ class Lattice:
         tid = ctypes.c_int()
         self._call("alm_add_turbine", ctypes.byref(d), ctypes.byref(tid))
         self.turbines.append(int(n_blades) * int(n_elements))
+        self._sink = None  # the library clears the loads sink when a rotor is added
         return tid.value
 
     def step(self, n=1):
@@ -312,6 +315,20 @@ class Lattice:
         lattice's stream; read it after an event recorded behind it."""
         assert out.dtype == self._torch().float64 and out.numel() == 2 and out.is_pinned()
         self._call("alm_get_loads_async", int(tid), ctypes.c_void_p(out.data_ptr()))
+
+    def set_loads_sink(self, ring):
+        """Have the device write each step's (thrust, torque) of every rotor
+        into `ring`, a page-locked float64 torch tensor of shape
+        (ring_len, n_turb, 2): step s lands in ring[s % ring_len] once step
+        s - 1 has finished on the stream.  None clears the sink."""
+        if ring is None:
+            self._call("alm_set_loads_sink", None, 0)
+            self._sink = None
+            return
+        assert ring.dtype == self._torch().float64 and ring.is_pinned() and ring.is_contiguous()
+        assert ring.dim() == 3 and ring.shape[1] == len(self.turbines) and ring.shape[2] == 2
+        self._call("alm_set_loads_sink", ctypes.c_void_p(ring.data_ptr()), int(ring.shape[0]))
+        self._sink = ring  # keep it alive while the device writes to it
 
     @staticmethod
     def _torch():

@@ -358,6 +358,28 @@ def test_async_loads_match_synchronous_reads():
     gs.destroy()
 
 
+def test_loads_sink_matches_synchronous_reads():
+    """With a zero-copy loads sink, the device writes each step's thrust and
+    torque into the page-locked ring; they equal the synchronising read of an
+    identical lattice, step after step.  A ring of the wrong shape is refused."""
+    import torch
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    gs, _ = setup_pair(dom, [turb], inflow=True)
+    ring = torch.zeros((3, 1, 2), dtype=torch.float64).pin_memory()
+    ga.set_loads_sink(ring)
+    for k in range(1, 9):
+        ga.step(1)
+        gs.step(1)
+        ga.sync()
+        if k >= 2:  # the loads of step k - 1 were evaluated during step k - 2, after the sink was set
+            assert tuple(ring[(k - 1) % 3, 0].tolist()) == gs.loads(0), k
+    with pytest.raises(AssertionError):
+        ga.set_loads_sink(torch.zeros((3, 2, 2), dtype=torch.float64).pin_memory())  # wrong rotor count
+    ga.destroy()
+    gs.destroy()
+
+
 def test_checkpoint_resume_is_bitwise():
     dom, turb = small_rotor_case()
     ga, _ = setup_pair(dom, [turb], inflow=True)
