@@ -101,7 +101,7 @@ struct StepArgs {
 // Planes a rotor tile covers at most (consecutive z-blocks of its column are
 // merged up to this depth), so that one CTA culls the blade elements once for
 // several planes and the rotor launch stays within one wave.
-constexpr int kRotorPlanes = 4;
+constexpr int kRotorPlanes = 3;
 
 // Work-list entry: bit 63 rotor tile, bits 56..62 planes - 1 (rotor tiles),
 // 48..55 lattice, 32..47 z, 16..31 y0, 0..15 x0.

@@ -1,6 +1,6 @@
 """The batched sweep at full size (16 seeded single-rotor lattices, 71.9 M
 cells) in the launch configurations the benchmark's tuner picks (32x4x1 with
-rotor tiles of 4 planes; 32x4x8, z-marching): one batched step from seeded
+rotor tiles of 3 planes; 32x4x8, z-marching): one batched step from seeded
 near-equilibrium states, checked against the FP64 oracle lattice by lattice on
 every element force and rotor load and on sampled cells (next to blade
 elements, inlet, outlet, bulk).

@@ -239,8 +239,9 @@ def test_full_size_single_turbine_sampled(kernel, tile):
 @pytest.mark.parametrize("tile", [(128, 1), (64, 2), (256, 1), (96, 1), (32, 8), (32, 4, 4), (32, 2, 7), (64, 2, 64),
                                   (32, 4, 2), (64, 1, 2)])
 def test_tile_shapes_agree(tile):
-    """Every CTA shape and marching depth, with rotor tiles merged over 1-4
-    planes (2-plane z-blocks merge in pairs), steps bitwise like the default."""
+    """Every CTA shape and marching depth (rotor tiles merged over up to 3
+    single-plane z-blocks, or one z-block of tile_z planes) steps bitwise like
+    the default."""
     dom, turb = small_rotor_case()
     ga, _ = setup_pair(dom, [turb], inflow=True)
     gb, _ = setup_pair(dom, [turb], inflow=True, tile=tile)
