@@ -43,11 +43,15 @@ def parse_args():
     p.add_argument("--tile", type=str, default="auto",
                    help="CTA tile XxY, XxYxZ or XxYxZxS (S = 1: rows staged in shared memory), or 'auto' "
                         "(the library's autotuner, cached)")
-    p.add_argument("--workload", choices=["single", "batch16", "precision", "warmstart", "tilesweep"], default="single",
+    p.add_argument("--workload", choices=["single", "batch16", "periodic", "precision", "warmstart", "tilesweep"],
+                   default="single",
                    help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices stepped by "
                         "the same two launches; precision: 512x256x256 rotor, FP32 vs BF16 vs FP16 storage, mean wake profiles; "
                         "warmstart: 3x3 farm, steps to a settled mean from a cold vs a surrogate warm start; "
-                        "tilesweep: the single-rotor workload at every tile candidate of the tuner")
+                        "tilesweep: the single-rotor workload at every tile candidate of the tuner; "
+                        "periodic: the 256x128x128 lattice periodic, without rotor or inlet, from a seeded "
+                        "near-equilibrium state (with --inplace: one PDF array, AA pattern)")
+    p.add_argument("--inplace", action="store_true", help="periodic workload on one PDF array (AA pattern)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--kernel", choices=["gauss", "roma"], default="gauss",
@@ -350,6 +354,20 @@ def run_ours(args):
         workload = WORKLOAD if args.kernel == "gauss" else WORKLOAD + "_roma"
         extra = {"rotor": "3 blades x 40 elements, D=32 at (64,64,64), TSR 6, "
                           + ("Gaussian eps=2" if args.kernel == "gauss" else "Roma 3-point delta")}
+    elif args.workload == "periodic":
+        nx, ny, nz = 256, 128, 128
+        lat = lbm.Lattice.create(nx, ny, nz, device=local, collision=args.collision, nu=1e-3, smag_c=0.1,
+                                 storage=args.storage, bc=("periodic",) * 3, tile=tile, diag_every=DIAG_EVERY,
+                                 inplace=args.inplace)
+        rho0, u0, fneq0 = I.random_state(nx, ny, nz, seed=I.DEFAULT_SEED + 9, u_mean=(0.05, 0.0, 0.0), du=0.01,
+                                         drho=0.005, fneq_amp=2e-4)
+        lat.init_fields(rho0, u0, fneq0)
+        del rho0, u0, fneq0
+        lattices = [lat]
+        workload = "periodic_256x128x128" + ("_inplace" if args.inplace else "")
+        extra = {"scheme": "AA pattern, one PDF array" if args.inplace else "pull, two PDF arrays",
+                 "pdf_bytes": 27 * nx * ny * nz * {"fp32": 4, "bf16": 2, "fp16": 2}[args.storage]
+                 * (1 if args.inplace else 2)}
     else:
         cases = I.batch_instances(16)
         cfgs = [dict(nx=d["nx"], ny=d["ny"], nz=d["nz"], collision=args.collision, nu=d["nu"], smag_c=d["smag_c"],
@@ -394,7 +412,7 @@ def run_ours(args):
     value = job_mlups(world, cells, args.steps, elapsed_ms)
     peak, peak_kind = load_peaks()
     achieved = achieved_gbs(bytes_per_cell, cells, kernel_ms * 1e-3)
-    thrust, torque = lat.loads(0)
+    thrust, torque = lat.loads(0) if lat.turbines else (None, None)
     diag_sums, diag_step = lat.diagnostics()
 
     # ---- end to end through the public API with host buffers

@@ -92,6 +92,12 @@ typedef struct {
                                 3-4 stage shared-memory ring filled by TMA bulk copies (needs
                                 tile_y = tile_z = 1 and nx a multiple of 4 (FP32) or 8 (16-bit));
                                 0 = direct loads */
+    int inplace;             /* 1: one PDF array updated in place (AA pattern: even steps pull from the
+                                neighbours and push into the slots they read, odd steps read and write a
+                                cell's own slots), half the PDF memory.  Needs periodic or no-slip faces,
+                                no rotor, single-plane direct tiles; the state read-out and write calls
+                                (moments, probe, PDFs, init, inflow, step counter) need an even step
+                                count, where the array equals the two-array scheme's.  0 = two arrays */
 } lbm_config;
 
 typedef struct {

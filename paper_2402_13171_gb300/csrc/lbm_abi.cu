@@ -67,6 +67,7 @@ struct Batch {
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [long?][start parity]
     unsigned n_rotor = 0;                 // rotor tiles at the head of the work list
     int rotor_planes = 1;                 // planes of the deepest rotor tile
+    int inplace = 0;                      // one PDF array, AA pattern
     long long* d_probe = nullptr;   // probe cell list and results, grown on demand
     double* d_probe_out = nullptr;
     int probe_cap = 0;
@@ -191,6 +192,18 @@ lbm_status validate_cfg(const lbm_config* c, std::string& msg)
         msg = "tile_x must be a multiple of 32, tile_x * tile_y <= 256, 1 <= tile_z <= 64";
         return LBM_ERR_INVALID_ARG;
     }
+    if (c->inplace != 0 && c->inplace != 1) { msg = "inplace must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
+    if (c->inplace) {
+        for (int a = 0; a < 3; ++a)
+            if (c->bc[a] != LBM_BC_PERIODIC && c->bc[a] != LBM_BC_NOSLIP) {
+                msg = "the in-place scheme takes periodic and no-slip faces only";
+                return LBM_ERR_UNSUPPORTED;
+            }
+        if (tz != 1 || c->staged) {
+            msg = "the in-place scheme takes single-plane direct tiles only";
+            return LBM_ERR_UNSUPPORTED;
+        }
+    }
     return LBM_OK;
 }
 
@@ -234,11 +247,12 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
         h.inflow_u[1] = u2 + 3 * (size_t)c.ny * c.nz;
     }
     const size_t fbytes = (size_t)h.N * 27 * store_bytes(b->store);
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < (c.inplace ? 1 : 2); ++p) {
         h.f[p] = dalloc(b, fbytes);
         if (!h.f[p]) return fail(b, LBM_ERR_OOM, "PDF array allocation failed");
         CK(cudaMemsetAsync(h.f[p], 0, fbytes, b->stream));  // offsets 0: f = w, the rest state
     }
+    if (c.inplace) h.f[1] = h.f[0];  // one array: both parities name it
     I.d_turb = (DevTurbine*)dalloc(b, sizeof(DevTurbine) * kMaxTurbines);
     void* ep = dalloc(b, sizeof(float4) * kMaxElements * 4);
     void* el = dalloc(b, sizeof(double) * 2 * kMaxElements);
@@ -396,6 +410,12 @@ lbm_status launch_one(Batch* b, int parity)
 {
     const StepArgs a = step_args(b, parity);
     const dim3 block(b->tile_x, b->tile_y);
+    if (b->inplace) {
+        StepArgs aa = a;
+        aa.write_step = 1;
+        CK(launch_step_aa(b->coll, b->store, dim3(b->n_tiles), block, b->stream, aa, parity == 1));
+        return LBM_OK;
+    }
     if (b->staged) {
         CK(launch_step(b->coll, b->store, dim3(std::min(b->n_tiles, b->staged_grid)), block, b->stream, a, false,
                        false));
@@ -453,8 +473,10 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     if (!out || n < 1 || n > kMaxInstances) return LBM_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         std::string msg;
-        if (validate_cfg(cfgs + i, msg) != LBM_OK) return LBM_ERR_INVALID_ARG;
+        const lbm_status v = validate_cfg(cfgs + i, msg);
+        if (v != LBM_OK) return v;
         if (cfgs[i].collision != cfgs[0].collision || cfgs[i].storage != cfgs[0].storage ||
+            cfgs[i].inplace != cfgs[0].inplace ||
             cfgs[i].cuda_stream != cfgs[0].cuda_stream || cfgs[i].tile_x != cfgs[0].tile_x ||
             cfgs[i].tile_y != cfgs[0].tile_y || cfgs[i].tile_z != cfgs[0].tile_z ||
             cfgs[i].diag_every != cfgs[0].diag_every)
@@ -471,6 +493,7 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     b->tile_y = cfgs[0].tile_y ? cfgs[0].tile_y : 4;
     b->tile_z = cfgs[0].tile_z ? cfgs[0].tile_z : 1;
     b->staged = 0;
+    b->inplace = cfgs[0].inplace;
     const int want_staged = cfgs[0].staged;
     b->diag_every = cfgs[0].diag_every;
     b->inst.resize(n);
@@ -560,9 +583,15 @@ const char* lbm_last_error(const lbm_ctx* ctx)
     (void)I;                                          \
     if (b->status != LBM_OK) return b->status;
 
+// In-place lattices hold the two-array state only after an even number of steps.
+#define REQUIRE_EVEN_STEP()                                                                                  \
+    if (b->inplace && (b->host_step & 1))                                                                    \
+        return fail(b, LBM_ERR_STATE, "in-place lattice: state access needs an even step count", false);
+
 lbm_status lbm_set_inflow(lbm_ctx* ctx, const lbm_inflow* in)
 {
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     if (!in || (in->kind != 0 && in->kind != 1)) return fail(b, LBM_ERR_INVALID_ARG, "bad inflow", false);
     if (in->kind == 1 && !(in->z0 > 0.0 && in->z_ref > in->z0))
         return fail(b, LBM_ERR_INVALID_ARG, "log law needs 0 < z0 < z_ref", false);
@@ -595,6 +624,7 @@ lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, con
 {
     NvtxRange nvtx_("lbm_init_fields");
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     const long long N = I.h.N;
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
@@ -635,6 +665,7 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
 {
     ENTER(ctx);
     if (!d) return fail(b, LBM_ERR_INVALID_ARG, "null turbine", false);
+    if (b->inplace) return fail(b, LBM_ERR_UNSUPPORTED, "the in-place scheme takes no rotor", false);
     if ((int)I.turb.size() >= kMaxTurbines) return fail(b, LBM_ERR_INVALID_ARG, "too many rotors", false);
     if (d->n_blades < 1 || d->n_elements < 1 || I.h.n_el + d->n_blades * d->n_elements > kMaxElements)
         return fail(b, LBM_ERR_INVALID_ARG, "element count out of range", false);
@@ -845,6 +876,7 @@ lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u)
 {
     NvtxRange nvtx_("lbm_get_moments");
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     if (!rho || !u) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
@@ -862,6 +894,7 @@ lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u)
 lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, double* u)
 {
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     if (n < 0 || (n > 0 && (!cells || !u))) return fail(b, LBM_ERR_INVALID_ARG, "bad probe arguments", false);
     if (n == 0) return LBM_OK;
     for (int k = 0; k < n; ++k)
@@ -900,6 +933,7 @@ lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f)
 {
     NvtxRange nvtx_("lbm_get_pdfs");
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
     const long long N = I.h.N;
     const void* src = I.h.f[b->host_step & 1];
@@ -928,6 +962,7 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f)
 {
     NvtxRange nvtx_("lbm_set_pdfs");
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null input", false);
     const long long N = I.h.N;
     std::vector<float> hf((size_t)27 * N);
@@ -1042,6 +1077,9 @@ lbm_status lbm_get_step(lbm_ctx* ctx, long long* step)
 lbm_status lbm_set_step(lbm_ctx* ctx, long long step)
 {
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
+    if (b->inplace && (step & 1))
+        return fail(b, LBM_ERR_STATE, "in-place lattice: the step count must stay even", false);
     if (step < 0) return fail(b, LBM_ERR_INVALID_ARG, "step < 0", false);
     if ((step & 1) != (b->host_step & 1)) {
         // keep the live state in array f[step & 1]
@@ -1072,6 +1110,8 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z, int st
     if (tile_x < 32 || tile_x % 32 != 0 || tile_y < 1 || tile_x * tile_y > 256 || tile_z < 1 || tile_z > 64)
         return fail(b, LBM_ERR_INVALID_ARG, "tile_x must be a multiple of 32, tile_x * tile_y <= 256, 1 <= tile_z <= 64",
                     false);
+    if (b->inplace && (tile_z != 1 || staged))
+        return fail(b, LBM_ERR_UNSUPPORTED, "the in-place scheme takes single-plane direct tiles only", false);
     if (staged && !staged_ok(b, tile_y, tile_z))
         return fail(b, LBM_ERR_INVALID_ARG, "staged rows need tile_y = tile_z = 1 and nx a multiple of 16 bytes", false);
     unsigned grid = 0;
@@ -1155,7 +1195,7 @@ std::string tune_key(Batch* b)
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
     std::string k = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "/" + std::to_string(b->coll) +
-                    "/" + std::to_string(b->store);
+                    "/" + std::to_string(b->store) + (b->inplace ? "/aa" : "");
     for (auto& I : b->inst) {
         k += "/" + std::to_string(I.h.nx) + "x" + std::to_string(I.h.ny) + "x" + std::to_string(I.h.nz);
         k += I.turb.empty() ? "" : "r" + std::to_string(I.turb.size());
@@ -1209,7 +1249,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
     for (int c = 0; s == LBM_OK && c < (int)(sizeof cand / sizeof cand[0]); ++c) {
         if (cand[c][3] && !staged_ok(b, cand[c][1], cand[c][2])) continue;
         s = lbm_set_tile(ctx, cand[c][0], cand[c][1], cand[c][2], cand[c][3]);
-        if (s == LBM_ERR_INVALID_ARG) {  // does not fit: skip the candidate
+        if (s == LBM_ERR_INVALID_ARG || s == LBM_ERR_UNSUPPORTED) {  // does not fit or not built: skip
             s = LBM_OK;
             continue;
         }
@@ -1290,7 +1330,7 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
     // the same split as launch_one
-    *launches = b->staged ? 1 : (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
+    *launches = (b->staged || b->inplace) ? 1 : (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
     return LBM_OK;
 }
 

@@ -121,6 +121,9 @@ __host__ __device__ inline int tile_planes(unsigned long long t) { return (int)(
 // and may overlap it (programmatic stream serialization).
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
                         bool dependent);
+// The in-place (AA) step over the whole work list: odd steps read and write a
+// cell's own slots, even steps pull and push across neighbours.
+cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd);
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
 int staged_blocks_per_sm(int coll, int store, int width);
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);

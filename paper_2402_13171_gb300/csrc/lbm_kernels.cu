@@ -42,6 +42,7 @@ __host__ __device__ constexpr float wq(int q) { return w1(qcx(q)) * w1(qcy(q)) *
 template <typename T> struct Io;
 template <> struct Io<float> {
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ldw(const float* p) { return *p; }
     static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
@@ -57,6 +58,7 @@ template <> struct Io<__nv_bfloat16> {
         return __uint_as_float((unsigned)v << 16);
     }
     static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
+    static __device__ __forceinline__ float ldw(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <> struct Io<__half> {
@@ -67,6 +69,7 @@ template <> struct Io<__half> {
         return __half2float(__ushort_as_half(v));
     }
     static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
+    static __device__ __forceinline__ float ldw(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -1000,6 +1003,51 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
 // carries none of the rotor path.  A CTA covers tile_x x tile_y cells of tile_z
 // consecutive planes; with MARCH a thread walks its column of planes and issues
 // the loads of the next plane before the collision of the current one.
+// The CTA's diagnostic partial sums (mass and momentum of its cells) into the
+// lattice's FP64 accumulators; the last CTA of the step, counted over all its
+// launches, publishes every lattice's sums with the step and flags non-finite
+// ones.  CTA-wide, on diagnostic steps only.
+__device__ __forceinline__ void diag_close(const StepArgs& A, const DevDomain* D, long long step, double m, double jx,
+                                           double jy, double jz, double (*s_red)[4])
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    double v[4] = {m, jx, jy, jz};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_red[tid >> 5][k] = v[k];
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < 4; ++k) {
+            double sum = 0.0;
+            for (int w = 0; w < (nthreads >> 5); ++w) sum += s_red[w][k];
+            atomicAdd(D->diag_acc + k, sum);
+        }
+        __threadfence();
+        const unsigned prev = atomicAdd(A.diag_done, 1u);
+        if (prev == A.n_total - 1u) {
+            __threadfence();
+            for (int i = 0; i < A.n_inst; ++i) {
+                const DevDomain* Di = A.dom + i;
+                bool finite = true;
+                for (int k = 0; k < 4; ++k) {
+                    const double sum = __ldcg(Di->diag_acc + k);
+                    Di->diag_res[k] = sum;
+                    Di->diag_acc[k] = 0.0;
+                    if (!isfinite(sum)) finite = false;
+                }
+                Di->diag_res[4] = (double)step;
+                if (!finite) atomicOr(Di->err, ERR_NONFINITE);
+            }
+            *A.diag_done = 0u;
+        }
+    }
+}
+
 // The rotor CTAs allow the dependent (bulk) launch to start as soon as they are
 // all running, so the two overlap and the actuator line of the next step,
 // evaluated by the last rotor CTA, runs under the bulk.  The two launches
@@ -1089,45 +1137,106 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
         }
     }
     // diagnostic step (uniform over the grid): FP64 sums, closed by the last CTA
-    if (diag) {
-        double v[4] = {o_m, o_jx, o_jy, o_jz};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
-        if ((tid & 31) == 0)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_red[tid >> 5][k] = v[k];
-        __syncthreads();
-        if (tid == 0) {
-            for (int k = 0; k < 4; ++k) {
-                double sum = 0.0;
-                for (int w = 0; w < (nthreads >> 5); ++w) sum += s_red[w][k];
-                atomicAdd(D->diag_acc + k, sum);
-            }
-            __threadfence();
-            const unsigned prev = atomicAdd(A.diag_done, 1u);
-            if (prev == A.n_total - 1u) {
-                __threadfence();
-                for (int i = 0; i < A.n_inst; ++i) {
-                    const DevDomain* Di = A.dom + i;
-                    bool finite = true;
-                    for (int k = 0; k < 4; ++k) {
-                        const double sum = __ldcg(Di->diag_acc + k);
-                        Di->diag_res[k] = sum;
-                        Di->diag_acc[k] = 0.0;
-                        if (!isfinite(sum)) finite = false;
-                    }
-                    Di->diag_res[4] = (double)step;
-                    if (!finite) atomicOr(Di->err, ERR_NONFINITE);
-                }
-                *A.diag_done = 0u;
-            }
-        }
-    }
+    if (diag) diag_close(A, D, step, o_m, o_jx, o_jy, o_jz, s_red);
     if constexpr (!ROTOR) {
         if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     }
+}
+
+// ------------------------------------------------------------------ in-place (AA) step
+
+// Source of a pull along one axis: wrapped on a periodic axis; -1 past a
+// no-slip wall (the only other face the in-place scheme takes).
+__device__ __forceinline__ int aa_src(int i, int n, int bc)
+{
+    if (i >= 0 && i < n) return i;
+    if (bc == BC_PERIODIC) return i < 0 ? i + n : i - n;
+    return -1;
+}
+
+// The time step on a single PDF array (the AA pattern), lattices with periodic
+// and no-slip faces and no rotor.  The array holds the pull scheme's state
+// A[q][x] = f*_q(x, n-1) before every even step:
+//  even step: pull h_q(x) = A[q][x - c_q] (bounce-back: A[qbar][x] at a wall),
+//    collide, and write f*_q(x, n) into the slot read for qbar,
+//    A[qbar][x + c_q], or into A[q][x] when x + c_q lies past a wall;
+//  odd step: h_q(x) = A[qbar][x], collide, write f*_q(x, n+1) to A[q][x].
+// Each slot is read and then written by one thread only, and after the odd
+// step the array is the pull scheme's state again, value for value.  One
+// launch per step; CTAs cover single-plane tiles.
+template <int COLL, typename T, bool ODD>
+__global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_step_aa(const StepArgs A)
+{
+    __shared__ double s_red[8][4];
+    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
+    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
+    const int x = (int)(tile & 0xFFFF) + threadIdx.x;
+    const DevDomain* D = A.dom + tile_lattice(tile);
+    const long long step = __ldcg(A.step_slot + A.parity);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        A.step_slot[A.parity ^ 1] = step + 1;
+        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
+    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;
+    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    const int nx = D->nx, ny = D->ny, nz = D->nz;
+    if (x < nx && y < ny) {
+        T* f = (T*)D->f[0];
+        const unsigned uN = (unsigned)D->N;
+        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+        float h[27];
+        if (ODD) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldw(f + ((unsigned)(26 - q) * uN + cell));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int sx = aa_src(x - qcx(q), nx, D->bc[0]), sy = aa_src(y - qcy(q), ny, D->bc[1]),
+                          sz = aa_src(z - qcz(q), nz, D->bc[2]);
+                if (sx < 0 || sy < 0 || sz < 0)
+                    h[q] = Io<T>::ldw(f + ((unsigned)(26 - q) * uN + cell));
+                else
+                    h[q] = Io<T>::ldw(f + ((unsigned)q * uN + ((unsigned)sz * (unsigned)ny + (unsigned)sy) * (unsigned)nx +
+                                           (unsigned)sx));
+            }
+        }
+        float m, jx, jy, jz;
+        if (COLL == COLL_CUMULANT)
+            collide_cumulant(h, D->body[0], D->body[1], D->body[2], D->omega, m, jx, jy, jz);
+        else
+            collide_srt_smag(h, D->body[0], D->body[1], D->body[2], D->tau0, D->smag_c2, m, jx, jy, jz);
+        if (diag) {
+            o_m = m;
+            o_jx = jx;
+            o_jy = jy;
+            o_jz = jz;
+        }
+        // opaque copies of the array pointer, plane size and cell index: the odd
+        // step stores to the addresses it loaded from, and without these the
+        // compiler keeps all 27 addresses live across the collision (and spills)
+        unsigned long long fa = (unsigned long long)f;
+        unsigned sN = uN, sc = cell;
+        asm volatile("" : "+l"(fa), "+r"(sN), "+r"(sc));
+        f = (T*)fa;
+        if (ODD) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Io<T>::st(f + ((unsigned)q * sN + sc), h[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int dx = aa_src(x + qcx(q), nx, D->bc[0]), dy = aa_src(y + qcy(q), ny, D->bc[1]),
+                          dz = aa_src(z + qcz(q), nz, D->bc[2]);
+                if (dx < 0 || dy < 0 || dz < 0)
+                    Io<T>::st(f + ((unsigned)q * sN + sc), h[q]);
+                else
+                    Io<T>::st(f + ((unsigned)(26 - q) * sN + ((unsigned)dz * (unsigned)ny + (unsigned)dy) * (unsigned)nx +
+                                   (unsigned)dx),
+                              h[q]);
+            }
+        }
+    }
+    if (diag) diag_close(A, D, step, o_m, o_jx, o_jy, o_jz, s_red);
 }
 
 // ------------------------------------------------------------------ staged step (TMA bulk copies)
@@ -1635,6 +1744,24 @@ static cudaError_t launch_dependent(void (*kernel)(StepArgs), dim3 grid, dim3 bl
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd)
+{
+#define LBM_AA_CASE(C, S, T)                                                \
+    if (coll == C && store == S) {                                          \
+        if (odd) k_step_aa<C, T, true><<<grid, block, 0, s>>>(a);           \
+        else k_step_aa<C, T, false><<<grid, block, 0, s>>>(a);              \
+        return cudaGetLastError();                                          \
+    }
+    LBM_AA_CASE(COLL_CUMULANT, STORE_FP32, float)
+    LBM_AA_CASE(COLL_CUMULANT, STORE_BF16, __nv_bfloat16)
+    LBM_AA_CASE(COLL_CUMULANT, STORE_FP16, __half)
+    LBM_AA_CASE(COLL_SRT_SMAG, STORE_FP32, float)
+    LBM_AA_CASE(COLL_SRT_SMAG, STORE_BF16, __nv_bfloat16)
+    LBM_AA_CASE(COLL_SRT_SMAG, STORE_FP16, __half)
+#undef LBM_AA_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,

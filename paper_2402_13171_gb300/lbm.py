@@ -45,6 +45,7 @@ class LbmConfig(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
         ("staged", ctypes.c_int),
+        ("inplace", ctypes.c_int),
     ]
 
 
@@ -154,7 +155,7 @@ class _TorchAllocator:
 
 def make_config(nx, ny, nz, collision="cumulant", nu=0.01, smag_c=0.0, storage="fp32",
                 bc=("periodic", "periodic", "periodic"), body_force=(0.0, 0.0, 0.0), seed=0, diag_every=0,
-                tile=(0, 0), stream_ptr=None, allocator=None) -> LbmConfig:
+                tile=(0, 0), stream_ptr=None, allocator=None, inplace=False) -> LbmConfig:
     c = LbmConfig()
     c.nx, c.ny, c.nz = int(nx), int(ny), int(nz)
     c.collision = COLL[collision] if isinstance(collision, str) else int(collision)
@@ -173,6 +174,7 @@ def make_config(nx, ny, nz, collision="cumulant", nu=0.01, smag_c=0.0, storage="
     c.tile_x, c.tile_y = int(tile[0]), int(tile[1])
     c.tile_z = int(tile[2]) if len(tile) > 2 else 0
     c.staged = int(tile[3]) if len(tile) > 3 else 0
+    c.inplace = int(bool(inplace))
     return c
 
 

@@ -1,7 +1,7 @@
 """Host-side argument checks of the C ABI, which run before any CUDA call:
 lattice sizes (including the 32-bit plane-offset limit 27 N < 2^31), boundary
-codes, viscosity, tiles, batches whose members disagree, and the rotor of the
-allocation-free actuator-line entry point."""
+codes, viscosity, tiles, batches whose members disagree, the in-place scheme's
+limits, and the rotor of the allocation-free actuator-line entry point."""
 import ctypes
 
 import pytest
@@ -98,3 +98,23 @@ def test_static_alm_rejects_bad_rotors_on_the_host(over):
     # the PDF, force and load pointers are only tested for NULL before the checks fail
     dummy = ctypes.c_void_p(256)
     assert fn(dummy, 64, 40, 40, None, ctypes.byref(d), 0, dummy, None, dummy, None) == INVALID_ARG
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(inplace=True, bc=("inout", "periodic", "periodic")), UNSUPPORTED),
+    (dict(inplace=True, bc=("periodic", "freeslip", "periodic")), UNSUPPORTED),
+    (dict(inplace=True, tile=(32, 4, 2)), UNSUPPORTED),
+    (dict(inplace=True, tile=(64, 1, 1, 1)), UNSUPPORTED),
+])
+def test_inplace_scheme_limits_are_checked_on_the_host(kw, code):
+    """The in-place (AA) scheme takes periodic and no-slip faces and
+    single-plane direct tiles only; anything else is refused at creation."""
+    assert _create(**kw) == code
+
+
+def test_inplace_flag_must_be_boolean():
+    L = lbm.load()
+    cfg = lbm.make_config(16, 16, 16)
+    cfg.inplace = 2
+    h = ctypes.c_void_p()
+    assert L.lbm_create(ctypes.byref(cfg), ctypes.byref(h)) == INVALID_ARG
