@@ -1145,22 +1145,77 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
 
 // ------------------------------------------------------------------ in-place (AA) step
 
-// Source of a pull along one axis: wrapped on a periodic axis; -1 past a
-// no-slip wall (the only other face the in-place scheme takes).
-__device__ __forceinline__ int aa_src(int i, int n, int bc)
+// Offset of the slot cell (x, y, z) reads for direction q on an even in-place
+// step: the pull source A[q][x - c_q], wrapped on periodic axes, or
+// A[qbar][x] when the source lies past a no-slip wall (bounce-back).  The cell
+// writes its post-collision f*_q to the slot it read for qbar: A[qbar][x + c_q],
+// or its own free slot A[q][x] when x + c_q lies past a wall.
+__device__ __forceinline__ unsigned aa_even_offset(const DevDomain* D, int q, int x, int y, int z)
 {
-    if (i >= 0 && i < n) return i;
-    if (bc == BC_PERIODIC) return i < 0 ? i + n : i - n;
-    return -1;
+    const int n[3] = {D->nx, D->ny, D->nz};
+    const int p[3] = {x, y, z};
+    const int c[3] = {qcx(q), qcy(q), qcz(q)};
+    int s[3];
+    for (int a = 0; a < 3; ++a) {
+        s[a] = p[a] - c[a];
+        if (s[a] < 0 || s[a] >= n[a]) {
+            if (D->bc[a] != BC_PERIODIC)
+                return (unsigned)(26 - q) * (unsigned)D->N + (((unsigned)z * (unsigned)n[1] + (unsigned)y) * (unsigned)n[0] + (unsigned)x);
+            s[a] += s[a] < 0 ? n[a] : -n[a];
+        }
+    }
+    return (unsigned)q * (unsigned)D->N + (((unsigned)s[2] * (unsigned)n[1] + (unsigned)s[1]) * (unsigned)n[0] + (unsigned)s[0]);
+}
+
+// The even step's loads and stores of a cell next to a no-slip wall, out of
+// line (few cells take them).
+template <typename T>
+__device__ __noinline__ void aa_wall_load(const DevDomain* D, const T* f, int x, int y, int z, float* h)
+{
+    for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldw(f + aa_even_offset(D, q, x, y, z));
+}
+template <typename T>
+__device__ __noinline__ void aa_wall_store(const DevDomain* D, T* f, int x, int y, int z, const float* h)
+{
+    for (int q = 0; q < 27; ++q) Io<T>::st(f + aa_even_offset(D, 26 - q, x, y, z), h[q]);
+}
+
+// Neighbour rows and columns of cell (x, y, z) for the even step away from
+// walls: source coordinates for c = -1, 0, +1 (wrapped on periodic axes), and
+// whether the cell touches a no-slip face.
+struct AaNbr {
+    unsigned xs[3], row[3][3];
+    bool wall;
+};
+__device__ __forceinline__ AaNbr aa_neighbours(const DevDomain* D, int x, int y, int z)
+{
+    const int nx = D->nx, ny = D->ny, nz = D->nz;
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    AaNbr r;
+    r.wall = false;
+    if (D->bc[0] == BC_PERIODIC) { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
+    else { r.wall = r.wall || x == 0 || x == nx - 1; }
+    if (D->bc[1] == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
+    else { r.wall = r.wall || y == 0 || y == ny - 1; }
+    if (D->bc[2] == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
+    else { r.wall = r.wall || z == 0 || z == nz - 1; }
+    r.xs[0] = (unsigned)xp; r.xs[1] = (unsigned)x; r.xs[2] = (unsigned)xm;
+    const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+    const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r.row[k][j] = (zs[k] * (unsigned)ny + ys[j]) * (unsigned)nx;
+    return r;
 }
 
 // The time step on a single PDF array (the AA pattern), lattices with periodic
 // and no-slip faces and no rotor.  The array holds the pull scheme's state
-// A[q][x] = f*_q(x, n-1) before every even step:
-//  even step: pull h_q(x) = A[q][x - c_q] (bounce-back: A[qbar][x] at a wall),
-//    collide, and write f*_q(x, n) into the slot read for qbar,
-//    A[qbar][x + c_q], or into A[q][x] when x + c_q lies past a wall;
-//  odd step: h_q(x) = A[qbar][x], collide, write f*_q(x, n+1) to A[q][x].
+// A[q][x] = f*_q(x, n-1) before every even step.  A cell reads its 27
+// populations from slots s_q, collides, and writes f*_q to the slot s_qbar it
+// read for the opposite direction:
+//  even step: s_q = the pull source (bounce-back at walls), aa_even_offset;
+//  odd step: s_q = A[qbar][x], so f*_q lands in A[q][x].
 // Each slot is read and then written by one thread only, and after the odd
 // step the array is the pull scheme's state again, value for value.  One
 // launch per step; CTAs cover single-plane tiles.
@@ -1180,25 +1235,27 @@ __global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_step_aa(
     }
     const bool diag = __ldcg(A.diag_flag + A.parity) != 0;
     float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
-    const int nx = D->nx, ny = D->ny, nz = D->nz;
-    if (x < nx && y < ny) {
+    if (x < D->nx && y < D->ny) {
         T* f = (T*)D->f[0];
         const unsigned uN = (unsigned)D->N;
-        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
         float h[27];
+        bool wall = false;
         if (ODD) {
+            const unsigned cell = ((unsigned)z * (unsigned)D->ny + (unsigned)y) * (unsigned)D->nx + (unsigned)x;
 #pragma unroll
             for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldw(f + ((unsigned)(26 - q) * uN + cell));
         } else {
+            const AaNbr nb = aa_neighbours(D, x, y, z);
+            wall = nb.wall;
+            if (!wall) {
 #pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const int sx = aa_src(x - qcx(q), nx, D->bc[0]), sy = aa_src(y - qcy(q), ny, D->bc[1]),
-                          sz = aa_src(z - qcz(q), nz, D->bc[2]);
-                if (sx < 0 || sy < 0 || sz < 0)
-                    h[q] = Io<T>::ldw(f + ((unsigned)(26 - q) * uN + cell));
-                else
-                    h[q] = Io<T>::ldw(f + ((unsigned)q * uN + ((unsigned)sz * (unsigned)ny + (unsigned)sy) * (unsigned)nx +
-                                           (unsigned)sx));
+                for (int q = 0; q < 27; ++q)
+                    h[q] = Io<T>::ldw(f + ((unsigned)q * uN + nb.row[q / 9][(q / 3) % 3] + nb.xs[q % 3]));
+            } else {
+                float hl[27];
+                aa_wall_load<T>(D, f, x, y, z, hl);
+#pragma unroll
+                for (int q = 0; q < 27; ++q) h[q] = hl[q];
             }
         }
         float m, jx, jy, jz;
@@ -1212,28 +1269,28 @@ __global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_step_aa(
             o_jy = jy;
             o_jz = jz;
         }
-        // opaque copies of the array pointer, plane size and cell index: the odd
-        // step stores to the addresses it loaded from, and without these the
-        // compiler keeps all 27 addresses live across the collision (and spills)
+        // the store slots are the load slots, recomputed from opaque copies of
+        // the inputs: kept live across the collision they would spill
         unsigned long long fa = (unsigned long long)f;
-        unsigned sN = uN, sc = cell;
-        asm volatile("" : "+l"(fa), "+r"(sN), "+r"(sc));
+        int xo = x, yo = y, zo = z;
+        asm volatile("" : "+l"(fa), "+r"(xo), "+r"(yo), "+r"(zo));
         f = (T*)fa;
         if (ODD) {
+            const unsigned cell = ((unsigned)zo * (unsigned)D->ny + (unsigned)yo) * (unsigned)D->nx + (unsigned)xo;
 #pragma unroll
-            for (int q = 0; q < 27; ++q) Io<T>::st(f + ((unsigned)q * sN + sc), h[q]);
-        } else {
+            for (int q = 0; q < 27; ++q) Io<T>::st(f + ((unsigned)q * uN + cell), h[q]);
+        } else if (!wall) {
+            const AaNbr nb = aa_neighbours(D, xo, yo, zo);
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
-                const int dx = aa_src(x + qcx(q), nx, D->bc[0]), dy = aa_src(y + qcy(q), ny, D->bc[1]),
-                          dz = aa_src(z + qcz(q), nz, D->bc[2]);
-                if (dx < 0 || dy < 0 || dz < 0)
-                    Io<T>::st(f + ((unsigned)q * sN + sc), h[q]);
-                else
-                    Io<T>::st(f + ((unsigned)(26 - q) * sN + ((unsigned)dz * (unsigned)ny + (unsigned)dy) * (unsigned)nx +
-                                   (unsigned)dx),
-                              h[q]);
+                const int p = 26 - q;  // the slot read for the opposite direction
+                Io<T>::st(f + ((unsigned)p * uN + nb.row[p / 9][(p / 3) % 3] + nb.xs[p % 3]), h[q]);
             }
+        } else {
+            float hl[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) hl[q] = h[q];
+            aa_wall_store<T>(D, f, xo, yo, zo, hl);
         }
     }
     if (diag) diag_close(A, D, step, o_m, o_jx, o_jy, o_jz, s_red);
