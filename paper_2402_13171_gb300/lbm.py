@@ -75,6 +75,12 @@ class LbmError(RuntimeError):
     pass
 
 
+def _require(ok, what):
+    """Argument check of the binding (kept under python -O, unlike assert)."""
+    if not ok:
+        raise ValueError(what)
+
+
 _lib = None
 
 
@@ -232,11 +238,11 @@ class Lattice:
         v = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
         g = None if fneq is None else np.ascontiguousarray(fneq, dtype=np.float32).reshape(-1)
         if r is not None:
-            assert r.size == self.N
+            _require(r.size == self.N, "rho needs nx*ny*nz values")
         if v is not None:
-            assert v.size == 3 * self.N
+            _require(v.size == 3 * self.N, "u needs 3*nx*ny*nz values")
         if g is not None:
-            assert g.size == 27 * self.N
+            _require(g.size == 27 * self.N, "fneq needs 27*nx*ny*nz values")
         self._call("lbm_init_fields", _p(r), _p(v), _p(g, _fp))
 
     def add_turbine(self, hub, radius, n_blades, n_elements, epsilon, omega, alpha, cl, cd, yaw=0.0, pitch=0.0,
@@ -297,7 +303,7 @@ class Lattice:
 
     def set_pdfs(self, f):
         a = np.ascontiguousarray(f, dtype=np.float64)
-        assert a.size == 27 * self.N
+        _require(a.size == 27 * self.N, "PDFs need 27*nx*ny*nz values")
         self._call("lbm_set_pdfs", _p(a))
 
     def loads(self, tid=0, elements=False):
@@ -315,7 +321,8 @@ class Lattice:
         """Enqueue the copy of the last enqueued step's (thrust, torque) into
         `out`, a page-locked float64 torch tensor of 2 elements, on the
         lattice's stream; read it after an event recorded behind it."""
-        assert out.dtype == self._torch().float64 and out.numel() == 2 and out.is_pinned()
+        _require(out.dtype == self._torch().float64 and out.numel() == 2 and out.is_pinned(),
+                 "out must be a page-locked float64 tensor of 2 elements")
         self._call("alm_get_loads_async", int(tid), ctypes.c_void_p(out.data_ptr()))
 
     def set_loads_sink(self, ring):
@@ -327,8 +334,10 @@ class Lattice:
             self._call("alm_set_loads_sink", None, 0)
             self._sink = None
             return
-        assert ring.dtype == self._torch().float64 and ring.is_pinned() and ring.is_contiguous()
-        assert ring.dim() == 3 and ring.shape[1] == len(self.turbines) and ring.shape[2] == 2
+        _require(ring.dtype == self._torch().float64 and ring.is_pinned() and ring.is_contiguous(),
+                 "the ring must be a contiguous page-locked float64 tensor")
+        _require(ring.dim() == 3 and ring.shape[1] == len(self.turbines) and ring.shape[2] == 2,
+                 "the ring must have shape (ring_len, rotors, 2)")
         self._call("alm_set_loads_sink", ctypes.c_void_p(ring.data_ptr()), int(ring.shape[0]))
         self._sink = ring  # keep it alive while the device writes to it
 

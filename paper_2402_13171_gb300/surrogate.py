@@ -94,7 +94,8 @@ class WakeMLP:
 
     def set_params(self, p):
         p = _f32(p)
-        assert p.size == self.n_params
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {p.size}")
         self._chk(self.L.mlp_set_params(self._h, p.ctypes.data_as(_fp)), "mlp_set_params")
 
     def params(self):

@@ -375,7 +375,7 @@ def test_loads_sink_matches_synchronous_reads():
         ga.sync()
         if k >= 2:  # the loads of step k - 1 were evaluated during step k - 2, after the sink was set
             assert tuple(ring[(k - 1) % 3, 0].tolist()) == gs.loads(0), k
-    with pytest.raises(AssertionError):
+    with pytest.raises(ValueError):
         ga.set_loads_sink(torch.zeros((3, 2, 2), dtype=torch.float64).pin_memory())  # wrong rotor count
     ga.destroy()
     gs.destroy()
