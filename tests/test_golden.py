@@ -46,7 +46,7 @@ def test_performance_model_of_sec4():
     import bench
     sc, rows = _read("performance_model_sec4.txt")
     assert bench.bytes_per_cell_update(force_components=3) == sc["n_b_bytes"]
-    # the fused gather of this build reads no force field
+    # the fused in-kernel gather reads no force field
     assert bench.bytes_per_cell_update() == 216
     assert bench.bytes_per_cell_update(elem_bytes=2) == 108
     l = bench.lightspeed(1713.0, sc["n_f_flops"], sc["a100_peak_tflops"] * 1e3, sc["n_b_bytes"])
