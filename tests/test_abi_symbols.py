@@ -51,3 +51,34 @@ def test_config_struct_matches_header_layout():
     assert pos == sorted(pos)
     fields = [f[0] for f in lbm.LbmConfig._fields_]
     assert [f for f in fields if f in order] == order
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every struct the binding mirrors (lbm_config, lbm_inflow,
+    alm_turbine_desc) has the size and field offsets the C compiler gives the
+    header's definition."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"lbm_config": lbm.LbmConfig, "lbm_inflow": lbm.LbmInflow, "alm_turbine_desc": lbm.AlmTurbineDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm_gb300.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(lbm.HERE), "include")
+    subprocess.run([gcc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, fname, v = line.split()
+        got[(cname, fname)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
