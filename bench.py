@@ -57,7 +57,12 @@ def parse_args():
     p.add_argument("--kernel", choices=["gauss", "roma"], default="gauss",
                    help="force regularisation of the single-rotor workload: the Gaussian (eps = 2) or Roma's "
                         "three-point delta")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.inplace and args.workload != "periodic":
+        p.error("--inplace applies to --workload periodic (the in-place scheme takes no rotor or inlet)")
+    if args.kernel != "gauss" and args.workload != "single":
+        p.error("--kernel applies to --workload single")
+    return args
 
 
 def dist_info():
