@@ -106,3 +106,24 @@ def test_inplace_halves_pdf_memory_and_refuses_what_it_does_not_take():
     ga.moments()                                      # even again: usable
     g2.destroy()
     ga.destroy()
+
+
+def test_inplace_batch_equals_separate_two_array_runs():
+    """Two in-place lattices of different sizes stepped as one batch match
+    their two-array runs bitwise at even step counts."""
+    shapes = [((20, 12, 9), ("periodic",) * 3), ((16, 10, 14), ("noslip", "periodic", "noslip"))]
+    cfgs = [dict(nx=s[0], ny=s[1], nz=s[2], nu=0.02, bc=bc, body_force=(1e-5, 0.0, 0.0), inplace=True)
+            for s, bc in shapes]
+    lat = lbm.batch_create(cfgs)
+    refs = []
+    for i, (L, (s, bc)) in enumerate(zip(lat, shapes)):
+        rho, u, fneq = I.random_state(*s, seed=40 + i, u_mean=(0.02, 0.0, 0.01), du=0.01, drho=0.005)
+        L.init_fields(rho, u, fneq)
+        g = lbm.Lattice.create(*s, nu=0.02, bc=bc, body_force=(1e-5, 0.0, 0.0))
+        g.init_fields(rho, u, fneq)
+        refs.append(g)
+    lat[0].step(6)
+    for L, g in zip(lat, refs):
+        g.step(6)
+        np.testing.assert_array_equal(L.pdfs(), g.pdfs())
+        g.destroy()
