@@ -353,9 +353,16 @@ class Sim:
         if rho is None:
             rho = np.ones(N)
         if u is None:
-            u = np.zeros((3, N))
+            # the mean inflow everywhere: uniform u_ref, or u_ref scaled by the
+            # log law ln(z_c/z0)/ln(z_ref/z0) at the cell-centre height z_c = z + 1/2
+            d = self.dom
+            scale = np.ones(d.nz)
+            if d.inflow_kind == 1:
+                scale = np.log((np.arange(d.nz) + 0.5) / d.z0) / np.log(d.z_ref / d.z0)
+            u = np.zeros((3, d.nz, d.ny * d.nx))
             for a in range(3):
-                u[a] = self.dom.u_ref[a]
+                u[a] = d.u_ref[a] * scale[:, None]
+            u = u.reshape(3, N)
         rho = _d(rho, N)
         u = _d(u, 3 * N)
         fn = None

@@ -137,3 +137,65 @@ def batch_instances(n=16, seed=DEFAULT_SEED + 3):
                                         seed=int(rng.integers(0, 2 ** 62)))
         out.append((dom, turb))
     return out
+
+
+def nonuniform_polars(fine_deg=0.25, coarse_deg=5.0, fine_range_deg=20.0):
+    """The synthetic rotor's polars (C_L = clip(2 pi alpha, +-1.2), C_D = 0.01 +
+    0.02 alpha^2) tabulated on unequally spaced angles, as real aerofoil tables
+    are: every fine_deg degrees on [-fine_range_deg, fine_range_deg], every
+    coarse_deg degrees beyond, over [-180, 180], plus the two stall corners
+    alpha = +-1.2 / (2 pi)."""
+    fine = np.arange(-fine_range_deg, fine_range_deg + 0.5 * fine_deg, fine_deg)
+    coarse = np.arange(-180.0, 180.0 + 0.5 * coarse_deg, coarse_deg)
+    coarse = coarse[np.abs(coarse) > fine_range_deg]
+    stall = np.degrees([-1.2 / (2 * math.pi), 1.2 / (2 * math.pi)])
+    deg = np.unique(np.round(np.concatenate([fine, coarse, stall]), 12))
+    alpha = np.radians(deg)
+    cl = np.clip(2 * math.pi * alpha, -1.2, 1.2)
+    cd = 0.01 + 0.02 * alpha ** 2
+    return alpha, cl, cd
+
+
+def blade_twist(n_elements, root=0.20, tip=0.02):
+    """Twist of element k (radians), linear from `root` at the blade root to
+    `tip` at the tip, at the element centres r_k = (k + 1/2) R / N_e."""
+    s = (np.arange(n_elements) + 0.5) / n_elements
+    return root + (tip - root) * s
+
+
+def yawed_twisted_rotor(nx=64, ny=40, nz=40, diameter=16.0, elements_per_blade=8, yaw_deg=7.0, pitch=0.05,
+                        seed=778, **kw):
+    """The scaled-down single-rotor case with every blade-geometry option on:
+    yaw yaw_deg degrees, a twist table, a collective pitch, and polars on
+    unequally spaced angles (nonuniform_polars)."""
+    dom, turb = single_turbine_case(nx, ny, nz, diameter=diameter, elements_per_blade=elements_per_blade, seed=seed,
+                                    yaw=math.radians(yaw_deg), **kw)
+    alpha, cl, cd = nonuniform_polars()
+    turb.update(alpha=alpha, cl=cl, cd=cd, pitch=float(pitch), twist=blade_twist(elements_per_blade),
+                theta0=0.3)
+    return dom, turb
+
+
+def log_law_profile(nz, u_hub, z0, z_hub):
+    """Mean streamwise inflow u(z) = u_hub ln(z_c / z0) / ln(z_hub / z0) at the
+    cell centres z_c = z + 1/2 above the bottom face."""
+    zc = np.arange(nz) + 0.5
+    return u_hub * np.log(zc / z0) / math.log(z_hub / z0)
+
+
+def small_farm_case(nx=96, ny=48, nz=40, diameter=12.0, elements_per_blade=6, u_hub=0.05, tsr=6.0,
+                    yaw_deg=(5.0, 9.0), x_hubs=(20.0, 60.0), seed=2402131715):
+    """A scaled-down version of the 3x3 farm: log-law inflow (z0 = 0.1, hub
+    height z_ref = nz / 2) with 1 % noise at the x inlet, zero-gradient outlet,
+    periodic y, free-slip bottom and top, and two yawed rotors in a row
+    (x_hubs, at mid-span and hub height)."""
+    z_hub = nz / 2.0
+    dom = dict(nx=nx, ny=ny, nz=nz, collision="cumulant", nu=1e-3, smag_c=0.1,
+               bc=("inout", "periodic", "freeslip"), body_force=(0.0, 0.0, 0.0), inflow_kind=1,
+               u_ref=(u_hub, 0.0, 0.0), z0=0.1, z_ref=z_hub, noise_rel=0.01, seed=seed)
+    turbs = []
+    for xh, yd in zip(x_hubs, yaw_deg):
+        turbs.append(single_turbine(nx, ny, nz, diameter=diameter, hub=(xh, ny / 2.0, z_hub),
+                                    elements_per_blade=elements_per_blade, tsr=tsr, u_inf=u_hub,
+                                    yaw=math.radians(yd)))
+    return dom, turbs

@@ -65,3 +65,31 @@ def test_random_state_is_seeded_and_bounded():
     assert np.all(np.abs(f1[13]) <= 2e-4 * 0.3 * (1 + 1e-6)) and np.all(np.abs(f1[0]) <= 2e-4 * 0.005 * (1 + 1e-6))
     r3, _, _ = I.random_state(9, 7, 5, seed=4)
     assert not np.array_equal(r1, r3)
+
+
+def test_unequal_polar_table_and_twist():
+    a, cl, cd = I.nonuniform_polars()
+    assert a[0] == pytest.approx(-math.pi) and a[-1] == pytest.approx(math.pi) and np.all(np.diff(a) > 0)
+    d = np.degrees(np.diff(a))
+    assert d.min() < 0.3 and d.max() == pytest.approx(5.0)
+    np.testing.assert_allclose(cl, np.clip(2 * math.pi * a, -1.2, 1.2), rtol=0, atol=0)
+    tw = I.blade_twist(8)
+    assert tw.shape == (8,) and np.all(np.diff(tw) < 0) and 0.02 < tw[-1] < tw[0] < 0.2
+
+
+def test_small_farm_recipe_and_rotor_supports():
+    """The scaled-down farm: log-law inflow referenced to hub height, free-slip
+    bottom and top, periodic y, two yawed rotors whose force supports
+    (hub +- (R sqrt(1 - e_axis_a^2) + 3 eps + 1)) lie inside [1, n - 2]."""
+    dom, turbs = I.small_farm_case()
+    assert dom["bc"] == ("inout", "periodic", "freeslip") and dom["inflow_kind"] == 1
+    assert dom["z_ref"] == dom["nz"] / 2 and len(turbs) == 2
+    n = (dom["nx"], dom["ny"], dom["nz"])
+    for t in turbs:
+        assert 0 < t["yaw"] < math.radians(10) and t["hub"][2] == dom["z_ref"]
+        ea = (math.cos(t["yaw"]), math.sin(t["yaw"]), 0.0)
+        for a in range(3):
+            ext = t["radius"] * math.sqrt(max(0.0, 1 - ea[a] ** 2)) + 3 * t["epsilon"] + 1
+            assert math.floor(t["hub"][a] - ext) >= 1 and math.ceil(t["hub"][a] + ext) <= n[a] - 2
+    prof = I.log_law_profile(dom["nz"], 0.05, 0.1, dom["z_ref"])
+    assert prof[int(dom["z_ref"] - 0.5)] < 0.05 < prof[int(dom["z_ref"] + 0.5)]

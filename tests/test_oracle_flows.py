@@ -165,6 +165,64 @@ def test_uniform_inflow_state_is_steady():
     np.testing.assert_allclose(s.f, f0, atol=2e-16)
 
 
+def _inflow(d, step, y, z):
+    return O.inflow_velocity(d, step, y, z)
+
+
+def test_log_law_inflow_profile():
+    """The farm's log-law inflow (a reading of the configuration): the mean
+    profile is zero at the roughness height z_c = z0, equals u_ref at z_c =
+    z_ref, and is logarithmic, rising by the same amount over every equal
+    ratio of heights (here 1/2, 3/2, 9/2, 27/2 at ratio 3, each step
+    u_ref ln 3 / ln(z_ref / z0)); at the three cell centres z_c = 2.5, 6.5 and
+    11.5 it is u_ref ln(z_c/z0)/ln(z_ref/z0)."""
+    u_ref, z0, z_ref = 0.05, 0.5, 13.5
+    d = O.make_domain(4, 3, 16, bc=("inout", "periodic", "freeslip"), inflow_kind=1, u_ref=(u_ref, 0, 0), z0=z0,
+                      z_ref=z_ref, noise_rel=0.0)
+    u = np.array([_inflow(d, 0, 1, z) for z in range(16)])
+    assert u[0, 0] == 0.0                                   # z_c = 0.5 = z0
+    assert u[13, 0] == pytest.approx(u_ref, rel=1e-15)     # z_c = 13.5 = z_ref
+    inc = u_ref * math.log(3.0) / math.log(z_ref / z0)
+    for z_lo, z_hi in ((0, 1), (1, 4), (4, 13)):            # z_c ratio 3
+        assert u[z_hi, 0] - u[z_lo, 0] == pytest.approx(inc, rel=1e-13)
+    for z in (2, 6, 11):
+        zc = z + 0.5
+        assert u[z, 0] == pytest.approx(u_ref * math.log(zc / z0) / math.log(z_ref / z0), rel=1e-14)
+    np.testing.assert_array_equal(u[:, 1:], 0.0)
+    assert np.all(np.diff(u[:, 0]) > 0)
+
+
+def test_log_law_inflow_shares_the_noise_of_the_uniform_inflow():
+    """The seeded noise does not depend on the mean profile: at every step,
+    column and component the log-law inflow minus the uniform one is exactly
+    the difference of the means, and the noise amplitude is noise_rel |u_ref|
+    at every height."""
+    kw = dict(bc=("inout", "periodic", "freeslip"), u_ref=(0.04, 0.01, 0.0), noise_rel=0.01, seed=99)
+    d_log = O.make_domain(4, 5, 12, inflow_kind=1, z0=0.1, z_ref=6.0, **kw)
+    d_uni = O.make_domain(4, 5, 12, inflow_kind=0, **kw)
+    amp = 0.01 * math.hypot(0.04, 0.01)
+    for step in (0, 3, 1000):
+        for y, z in ((0, 0), (2, 5), (4, 11)):
+            scale = math.log((z + 0.5) / 0.1) / math.log(6.0 / 0.1)
+            ul, uu = _inflow(d_log, step, y, z), _inflow(d_uni, step, y, z)
+            np.testing.assert_allclose(ul - uu, np.array([0.04, 0.01, 0.0]) * (scale - 1.0), rtol=0, atol=1e-17)
+            assert np.all(np.abs(uu - np.array([0.04, 0.01, 0.0])) <= amp)
+
+
+def test_log_law_initial_state_is_the_mean_profile():
+    """With no velocity given the oracle starts from the equilibrium of the
+    mean inflow, the log profile on a log-law lattice."""
+    d = O.make_domain(5, 3, 10, bc=("inout", "periodic", "freeslip"), inflow_kind=1, u_ref=(0.05, 0, 0), z0=0.1,
+                      z_ref=5.0, noise_rel=0.0)
+    s = O.Sim(d)
+    s.init_fields()
+    rho, u = s.moments()
+    prof = I.log_law_profile(10, 0.05, 0.1, 5.0)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-15)
+    np.testing.assert_allclose(u[0], np.broadcast_to(prof[:, None, None], u[0].shape), atol=1e-16)
+    np.testing.assert_allclose(u[1:], 0.0, atol=1e-16)
+
+
 def test_mass_and_momentum_conserved_periodic():
     rng_state = I.random_state(6, 5, 7, seed=99, u_mean=(0.02, -0.01, 0.01))
     for coll in ("cumulant", "srt_smag"):
