@@ -436,31 +436,41 @@ def run_ours(args):
         # each step's loads are written by the device straight into page-locked
         # memory (no copy on the stream) and read one step behind, so the host
         # never waits on the step it has just enqueued
+        rho_o = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        u_o = torch.empty(3 * N, dtype=torch.float64).pin_memory().numpy()
         ring = torch.zeros((4, 1, 2), dtype=torch.float64).pin_memory()
         ring_np = ring.numpy()
         evs = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def e2e_pass(k):
+            lat.init_fields(rho_h, u_h)
+            lat.set_loads_sink(ring)
+            s0 = lat.step_count()
+            loads = None
+            for i in range(k):
+                lat.step(1)
+                evs[i % 2].record(lat.stream)
+                if i > 0:
+                    evs[(i - 1) % 2].synchronize()
+                    loads = ring_np[(s0 + i) % 4, 0].tolist()
+            evs[(k - 1) % 2].synchronize()
+            loads = ring_np[(s0 + k) % 4, 0].tolist()
+            lat.moments(rho_o, u_o)
+            return loads
+
+        e2e_pass(min(args.warmup, args.steps))   # untimed: first-use staging allocations
         barrier()
         t = time.perf_counter()
-        lat.init_fields(rho_h, u_h)
-        lat.set_loads_sink(ring)
-        s0 = lat.step_count()
-        for i in range(args.steps):
-            lat.step(1)
-            evs[i % 2].record(lat.stream)
-            if i > 0:
-                evs[(i - 1) % 2].synchronize()
-                last_loads = ring_np[(s0 + i) % 4, 0].tolist()
-        evs[(args.steps - 1) % 2].synchronize()
-        last_loads = ring_np[(s0 + args.steps) % 4, 0].tolist()
-        rho_o, u_o = lat.moments()
+        last_loads = e2e_pass(args.steps)
         barrier()
         dt = time.perf_counter() - t
         dt = reduce_max([dt], dist, device="cuda")[0]
         e2e = {"value": job_mlups(world, cells, args.steps, dt * 1e3), "unit": "MLUPS",
-               "h2d_bytes_per_step": 16.0 * N / args.steps,
+               "h2d_bytes_per_step": 32.0 * N / args.steps,
                "d2h_bytes_per_step": 16.0 + 32.0 * N / args.steps,
-               "api": "lbm_init_fields(host rho, u) + alm_set_loads_sink(page-locked ring) + K x (lbm_step(1), "
-                      "read that step's thrust and torque from the ring one step behind) + lbm_get_moments",
+               "api": "lbm_init_fields(page-locked FP64 rho, u) + alm_set_loads_sink(page-locked ring) + K x "
+                      "(lbm_step(1), read that step's thrust and torque from the ring one step behind) + "
+                      "lbm_get_moments(into page-locked FP64 rho, u); after one untimed pass of the same calls",
                "last_loads": last_loads}
 
     acc = None

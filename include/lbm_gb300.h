@@ -193,10 +193,41 @@ lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u);
  * copying whole fields.  Synchronises. */
 lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, double* u);
 
-/* Absolute populations f [27][N] (host, FP64) / overwrite them (checkpoint
- * restore: the step counter and lagged ALM force are kept).  Synchronises. */
+/* Absolute populations f [27][N] (host, FP64) / overwrite them (the step
+ * counter and the lagged ALM force are kept; the actuator line of the current
+ * step is re-evaluated).  Conversion runs on the device, plane by plane, in a
+ * reused staging buffer.  Synchronises.  For a bitwise resume use
+ * lbm_get_state / lbm_set_state. */
 lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f);
 lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f);
+
+/* Checkpoint of one lattice, for a bitwise resume: everything a time step
+ * reads that is not a descriptor -- the raw PDF array of the current step in
+ * the storage type, each rotor's lagged force box (the ALM force of the last
+ * collision, which the next sampling of Sec. 2.2 reads), the actuator-line
+ * element buffers and FP64 rotor loads of both step parities, the inlet
+ * velocity columns of both parities, the last diagnostic sums -- and the
+ * step counter, behind a header with the lattice's shape.  The blob is
+ * host memory owned by the caller: lbm_get_state_size gives its size,
+ * lbm_get_state fills it, lbm_set_state restores it into a lattice of the
+ * same sizes, storage, collision, boundary rules and rotors (INVALID_ARG
+ * otherwise) and sets the step counter (for a batch: restore every member
+ * from states taken at the same step).  A run resumed from it continues
+ * bit for bit as the original.  In-place lattices need an even step count
+ * (STATE otherwise).  get/set synchronise. */
+lbm_status lbm_get_state_size(lbm_ctx* ctx, size_t* bytes);
+lbm_status lbm_get_state(lbm_ctx* ctx, void* buf, size_t bytes);
+lbm_status lbm_set_state(lbm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Bound of the staged step's waits on its own TMA copies, in SM clock cycles
+ * (default 2^31, about 1 s; the bounded waits of Sec. 2.1's streaming are an
+ * implementation matter, not the paper's).  A wait that passes it sets
+ * LBM_ERR_TIMEOUT, reported by the next synchronising call; the kernel first
+ * waits, with the default bound, for the copies it still has in flight.
+ * Meant for tests of that error path: with a bound of 0 every wait gives up
+ * before it looks, on copies that are valid and land a little later.
+ * INVALID_ARG for a negative bound. */
+lbm_status lbm_set_wait_limit(lbm_ctx* ctx, long long cycles);
 
 /* Rotor thrust and torque (FP64 sums, Sec. 2.2) of the forces applied in the
  * last completed step; optionally the element blade forces and positions
@@ -286,14 +317,18 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches);
  *   elem_force   device, 3 floats per element (blade-major): blade forces
  *   elem_pos     device, 3 floats per element, or NULL
  *   loads        device, 2 doubles: thrust, torque
- * Work is enqueued on cuda_stream (NULL = legacy default stream); the call
- * returns without waiting.  Nothing is allocated: the scratch is one static
+ * Work is enqueued on cuda_stream (NULL = legacy default stream).  The rotor
+ * descriptor and polar table are copied from pageable host memory, so the
+ * call may wait for earlier work on that stream before it returns; the
+ * outputs are complete once the stream has passed the call's work.  Nothing
+ * is allocated: the scratch is one static
  * device block of about 300 KB that every GPU loading this library holds
  * until the process exits.  Limits: at most 1024 elements and 8192 polar
  * points (INVALID_ARG beyond, before anything is enqueued).  The first call
  * on a device looks up the block's address (make it before any stream
  * capture).  All calls share the block: calls that overlap on the GPU race.
- * Errors: INVALID_ARG, CUDA. */
+ * Errors: INVALID_ARG (also for non-finite rotor inputs or body force, and
+ * blade or element counts whose product exceeds the limit), CUDA. */
 lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, int nz, const double body_force[3],
                            const alm_turbine_desc* desc, long long step, float* elem_force, float* elem_pos,
                            double* loads, void* cuda_stream);

@@ -71,6 +71,9 @@ struct Batch {
     long long* d_probe = nullptr;   // probe cell list and results, grown on demand
     double* d_probe_out = nullptr;
     int probe_cap = 0;
+    void* d_stage = nullptr;        // staging for host input/output, grown on demand and reused
+    size_t stage_cap = 0;
+    long long wait_cycles = kDefaultWaitCycles;  // bound of the staged step's copy-barrier waits
 };
 
 }  // namespace
@@ -386,6 +389,7 @@ StepArgs step_args(Batch* b, int parity)
     a.diag_every = b->diag_every;
     a.tile_z = b->tile_z;
     a.staged = b->staged;
+    a.wait_cycles = b->wait_cycles;
     return a;
 }
 
@@ -452,6 +456,20 @@ lbm_status zero_fbox(Batch* b, Instance& I)
 {
     for (auto& t : I.turb) CK(cudaMemsetAsync(t.dev.fbox, 0, sizeof(float) * 3 * t.dev.bcells, b->stream));
     return LBM_OK;
+}
+
+// Device staging buffer of at least `bytes` (> 0), reused across calls (stream-ordered).
+void* stage(Batch* b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (bytes > b->stage_cap) {
+        if (b->d_stage) dfree(b, b->d_stage);
+        b->stage_cap = 0;
+        b->d_stage = dalloc(b, bytes);
+        if (!b->d_stage) return nullptr;
+        b->stage_cap = bytes;
+    }
+    return b->d_stage;
 }
 
 lbm_status check_device_errors(Batch* b)
@@ -625,40 +643,29 @@ lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, con
     NvtxRange nvtx_("lbm_init_fields");
     ENTER(ctx);
     REQUIRE_EVEN_STEP();
-    const long long N = I.h.N;
+    const size_t N = (size_t)I.h.N;
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
-    std::vector<float> hd, hu;
-    float *d_drho = nullptr, *d_u = nullptr, *d_fneq = nullptr;
-    if (rho) {
-        hd.resize(N);
-        for (long long i = 0; i < N; ++i) hd[i] = (float)(rho[i] - 1.0);
-        d_drho = (float*)dalloc(b, sizeof(float) * N);
-        if (!d_drho) return fail(b, LBM_ERR_OOM, "staging allocation failed");
-        CK(cudaMemcpyAsync(d_drho, hd.data(), sizeof(float) * N, cudaMemcpyHostToDevice, b->stream));
-    }
-    if (u) {
-        hu.resize(3 * N);
-        for (long long i = 0; i < 3 * N; ++i) hu[i] = (float)u[i];
-        d_u = (float*)dalloc(b, sizeof(float) * 3 * N);
-        if (!d_u) return fail(b, LBM_ERR_OOM, "staging allocation failed");
-        CK(cudaMemcpyAsync(d_u, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice, b->stream));
-    }
-    if (fneq) {
-        d_fneq = (float*)dalloc(b, sizeof(float) * 27 * N);
-        if (!d_fneq) return fail(b, LBM_ERR_OOM, "staging allocation failed");
-        CK(cudaMemcpyAsync(d_fneq, fneq, sizeof(float) * 27 * N, cudaMemcpyHostToDevice, b->stream));
-    }
+    // the caller's arrays go to the device as they are (FP64 rho, u; FP32 fneq)
+    // and are converted there
+    const size_t b_rho = rho ? 8 * N : 0, b_u = u ? 24 * N : 0, b_f = fneq ? 4 * 27 * N : 0;
+    char* st = (char*)stage(b, b_rho + b_u + b_f);
+    if (!st) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+    const double* d_rho = rho ? (const double*)st : nullptr;
+    const double* d_u = u ? (const double*)(st + b_rho) : nullptr;
+    const float* d_fneq = fneq ? (const float*)(st + b_rho + b_u) : nullptr;
+    if (rho) CK(cudaMemcpyAsync((void*)d_rho, rho, b_rho, cudaMemcpyHostToDevice, b->stream));
+    if (u) CK(cudaMemcpyAsync((void*)d_u, u, b_u, cudaMemcpyHostToDevice, b->stream));
+    if (fneq) CK(cudaMemcpyAsync((void*)d_fneq, fneq, b_f, cudaMemcpyHostToDevice, b->stream));
     const int par = (int)(b->host_step & 1);
-    CK(launch_init(b->store, b->d_dom + ctx->idx, I.h, d_drho, d_u, d_fneq, par, 1, b->stream));
-    if (b->stream) CK(cudaStreamSynchronize(b->stream));
-    else CK(cudaDeviceSynchronize());
-    dfree(b, d_drho);
-    dfree(b, d_u);
-    dfree(b, d_fneq);
+    CK(launch_init(b->store, b->d_dom + ctx->idx, I.h, d_rho, d_u, d_fneq, par, 1, b->stream));
     s = zero_fbox(b, I);
     if (s != LBM_OK) return s;
-    return refresh_alm(b);
+    s = refresh_alm(b);
+    if (s != LBM_OK) return s;
+    if (b->stream) CK(cudaStreamSynchronize(b->stream));
+    else CK(cudaDeviceSynchronize());
+    return LBM_OK;
 }
 
 lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
@@ -667,7 +674,7 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     if (!d) return fail(b, LBM_ERR_INVALID_ARG, "null turbine", false);
     if (b->inplace) return fail(b, LBM_ERR_UNSUPPORTED, "the in-place scheme takes no rotor", false);
     if ((int)I.turb.size() >= kMaxTurbines) return fail(b, LBM_ERR_INVALID_ARG, "too many rotors", false);
-    if (d->n_blades < 1 || d->n_elements < 1 || I.h.n_el + d->n_blades * d->n_elements > kMaxElements)
+    if (!turbine_counts_ok(d, kMaxElements) || I.h.n_el + d->n_blades * d->n_elements > kMaxElements)
         return fail(b, LBM_ERR_INVALID_ARG, "element count out of range", false);
     if (d->regularisation != ALM_REG_GAUSSIAN && d->regularisation != ALM_REG_ROMA)
         return fail(b, LBM_ERR_INVALID_ARG, "unknown regularisation", false);
@@ -679,6 +686,7 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
     if (d->n_polar < 2 || !d->alpha || !d->cl || !d->cd) return fail(b, LBM_ERR_INVALID_ARG, "polar table missing", false);
     for (int i = 1; i < d->n_polar; ++i)
         if (!(d->alpha[i] > d->alpha[i - 1])) return fail(b, LBM_ERR_INVALID_ARG, "alpha must ascend", false);
+    if (!turbine_values_finite(d)) return fail(b, LBM_ERR_INVALID_ARG, "non-finite rotor input", false);
     TurbineHost t;
     t.desc = *d;
     t.alpha.assign(d->alpha, d->alpha + d->n_polar);
@@ -881,14 +889,12 @@ lbm_status lbm_get_moments(lbm_ctx* ctx, double* rho, double* u)
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
     const long long N = I.h.N;
-    double* d = (double*)dalloc(b, sizeof(double) * 4 * N);
+    double* d = (double*)stage(b, sizeof(double) * 4 * N);
     if (!d) return fail(b, LBM_ERR_OOM, "moment buffer allocation failed");
     CK(launch_moments(b->store, b->d_dom + ctx->idx, I.h, (int)(b->host_step & 1), d, d + N, b->stream));
     CK(cudaMemcpyAsync(rho, d, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream));
     CK(cudaMemcpyAsync(u, d + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, b->stream));
-    s = check_device_errors(b);
-    dfree(b, d);
-    return s;
+    return check_device_errors(b);
 }
 
 lbm_status lbm_probe(lbm_ctx* ctx, const long long* cells, int n, double* rho, double* u)
@@ -936,26 +942,15 @@ lbm_status lbm_get_pdfs(lbm_ctx* ctx, double* f)
     REQUIRE_EVEN_STEP();
     if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
     const long long N = I.h.N;
-    const void* src = I.h.f[b->host_step & 1];
-    std::vector<float> hf((size_t)27 * N);
-    if (b->store == STORE_FP32) {
-        CK(cudaMemcpyAsync(hf.data(), src, sizeof(float) * 27 * N, cudaMemcpyDeviceToHost, b->stream));
-    } else {
-        float* d = (float*)dalloc(b, sizeof(float) * 27 * N);
-        if (!d) return fail(b, LBM_ERR_OOM, "staging allocation failed");
-        CK(launch_to_float(b->store, src, d, 27 * N, b->stream));
-        CK(cudaMemcpyAsync(hf.data(), d, sizeof(float) * 27 * N, cudaMemcpyDeviceToHost, b->stream));
-        lbm_status s = check_device_errors(b);
-        dfree(b, d);
-        if (s != LBM_OK) return s;
-    }
-    lbm_status s = check_device_errors(b);
-    if (s != LBM_OK) return s;
+    const char* src = (const char*)I.h.f[b->host_step & 1];
+    double* d = (double*)stage(b, sizeof(double) * N);
+    if (!d) return fail(b, LBM_ERR_OOM, "staging allocation failed");
+    // plane by plane: w_q + h on the device, then one copy to the caller's array
     for (int q = 0; q < 27; ++q) {
-        const double w = wqh(q);
-        for (long long i = 0; i < N; ++i) f[(size_t)q * N + i] = w + (double)hf[(size_t)q * N + i];
+        CK(launch_plane_to_f64(b->store, src + (size_t)q * N * store_bytes(b->store), d, N, wqh(q), b->stream));
+        CK(cudaMemcpyAsync(f + (size_t)q * N, d, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream));
     }
-    return LBM_OK;
+    return check_device_errors(b);
 }
 
 lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f)
@@ -965,25 +960,16 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f)
     REQUIRE_EVEN_STEP();
     if (!f) return fail(b, LBM_ERR_INVALID_ARG, "null input", false);
     const long long N = I.h.N;
-    std::vector<float> hf((size_t)27 * N);
+    char* dst = (char*)I.h.f[b->host_step & 1];
+    double* d = (double*)stage(b, sizeof(double) * N);
+    if (!d) return fail(b, LBM_ERR_OOM, "staging allocation failed");
     for (int q = 0; q < 27; ++q) {
-        const double w = wqh(q);
-        for (long long i = 0; i < N; ++i) hf[(size_t)q * N + i] = (float)(f[(size_t)q * N + i] - w);
+        CK(cudaMemcpyAsync(d, f + (size_t)q * N, sizeof(double) * N, cudaMemcpyHostToDevice, b->stream));
+        CK(launch_plane_from_f64(b->store, d, dst + (size_t)q * N * store_bytes(b->store), N, wqh(q), b->stream));
     }
-    void* dst = I.h.f[b->host_step & 1];
-    if (b->store == STORE_FP32) {
-        CK(cudaMemcpyAsync(dst, hf.data(), sizeof(float) * 27 * N, cudaMemcpyHostToDevice, b->stream));
-        if (b->stream) CK(cudaStreamSynchronize(b->stream));
-    } else {
-        float* d = (float*)dalloc(b, sizeof(float) * 27 * N);
-        if (!d) return fail(b, LBM_ERR_OOM, "staging allocation failed");
-        CK(cudaMemcpyAsync(d, hf.data(), sizeof(float) * 27 * N, cudaMemcpyHostToDevice, b->stream));
-        CK(launch_from_float(b->store, d, dst, 27 * N, b->stream));
-        if (b->stream) CK(cudaStreamSynchronize(b->stream));
-        else CK(cudaDeviceSynchronize());
-        dfree(b, d);
-    }
-    return refresh_alm(b);
+    lbm_status s = refresh_alm(b);
+    if (s != LBM_OK) return s;
+    return check_device_errors(b);
 }
 
 lbm_status alm_get_loads(lbm_ctx* ctx, int id, double* thrust, double* torque, float* elem_force, float* elem_pos)
@@ -1091,6 +1077,148 @@ lbm_status lbm_set_step(lbm_ctx* ctx, long long step)
     lbm_status s = refresh_alm(b);
     if (s != LBM_OK) return s;
     return check_device_errors(b);
+}
+
+// ---------------------------------------------------------------- checkpoints
+
+namespace {
+
+// Header of a checkpoint blob; the sections follow in the order of
+// state_sections().
+struct StateHeader {
+    char magic[8];
+    int version;
+    int nx, ny, nz, storage, collision, inplace;
+    int bc[3];
+    int n_turb, n_el;
+    long long step;
+    long long bcells[kMaxTurbines];
+    unsigned long long bytes;  // whole blob
+};
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+
+struct Section {
+    void* dev;
+    size_t bytes;
+};
+
+// The device state one step reads and writes, beyond the descriptors: the
+// PDFs of the current step, each rotor's lagged force box, the actuator-line
+// element buffers and rotor loads of both step parities, the inlet columns of
+// both parities, and the last diagnostic sums.
+std::vector<Section> state_sections(Batch* b, Instance& I)
+{
+    std::vector<Section> v;
+    const DevDomain& h = I.h;
+    v.push_back({h.f[b->host_step & 1], (size_t)h.N * 27 * store_bytes(b->store)});
+    for (auto& t : I.turb) v.push_back({t.dev.fbox, sizeof(float) * 3 * (size_t)t.dev.bcells});
+    if (h.n_el > 0)
+        for (int p = 0; p < 2; ++p) {
+            v.push_back({h.el_pos[p], sizeof(float4) * h.n_el});
+            v.push_back({h.el_force[p], sizeof(float4) * h.n_el});
+        }
+    if (h.n_turb > 0)
+        for (int p = 0; p < 2; ++p) v.push_back({h.loads[p], sizeof(double) * 2 * h.n_turb});
+    if (h.inflow_u[0])
+        for (int p = 0; p < 2; ++p) v.push_back({h.inflow_u[p], sizeof(float) * 3 * (size_t)h.ny * h.nz});
+    v.push_back({h.diag_res, sizeof(double) * 5});
+    return v;
+}
+
+StateHeader state_header(Batch* b, Instance& I)
+{
+    StateHeader H{};
+    std::memcpy(H.magic, kStateMagic, 8);
+    H.version = 1;
+    H.nx = I.h.nx;
+    H.ny = I.h.ny;
+    H.nz = I.h.nz;
+    H.storage = b->store;
+    H.collision = b->coll;
+    H.inplace = b->inplace;
+    for (int a = 0; a < 3; ++a) H.bc[a] = I.h.bc[a];
+    H.n_turb = I.h.n_turb;
+    H.n_el = I.h.n_el;
+    H.step = b->host_step;
+    for (size_t t = 0; t < I.turb.size(); ++t) H.bcells[t] = I.turb[t].dev.bcells;
+    size_t bytes = sizeof(StateHeader);
+    for (auto& sec : state_sections(b, I)) bytes += sec.bytes;
+    H.bytes = bytes;
+    return H;
+}
+
+}  // namespace
+
+lbm_status lbm_get_state_size(lbm_ctx* ctx, size_t* bytes)
+{
+    ENTER(ctx);
+    if (!bytes) return fail(b, LBM_ERR_INVALID_ARG, "null output", false);
+    *bytes = (size_t)state_header(b, I).bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_ctx* ctx, void* buf, size_t bytes)
+{
+    NvtxRange nvtx_("lbm_get_state");
+    ENTER(ctx);
+    REQUIRE_EVEN_STEP();
+    const StateHeader H = state_header(b, I);
+    if (!buf || bytes < H.bytes) return fail(b, LBM_ERR_INVALID_ARG, "state buffer missing or too small", false);
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    std::memcpy(buf, &H, sizeof H);
+    char* p = (char*)buf + sizeof H;
+    for (auto& sec : state_sections(b, I)) {
+        CK(cudaMemcpyAsync(p, sec.dev, sec.bytes, cudaMemcpyDeviceToHost, b->stream));
+        p += sec.bytes;
+    }
+    return check_device_errors(b);
+}
+
+lbm_status lbm_set_state(lbm_ctx* ctx, const void* buf, size_t bytes)
+{
+    NvtxRange nvtx_("lbm_set_state");
+    ENTER(ctx);
+    REQUIRE_EVEN_STEP();
+    if (!buf || bytes < sizeof(StateHeader)) return fail(b, LBM_ERR_INVALID_ARG, "state buffer missing or too small", false);
+    StateHeader H;
+    std::memcpy(&H, buf, sizeof H);
+    const StateHeader mine = state_header(b, I);
+    bool same = std::memcmp(H.magic, kStateMagic, 8) == 0 && H.version == 1 && H.nx == mine.nx && H.ny == mine.ny &&
+                H.nz == mine.nz && H.storage == mine.storage && H.collision == mine.collision &&
+                H.inplace == mine.inplace && H.n_turb == mine.n_turb && H.n_el == mine.n_el && H.bytes == mine.bytes;
+    for (int a = 0; a < 3; ++a) same = same && H.bc[a] == mine.bc[a];
+    for (int t = 0; t < kMaxTurbines; ++t) same = same && H.bcells[t] == mine.bcells[t];
+    if (!same) return fail(b, LBM_ERR_INVALID_ARG, "state was taken from a lattice of another shape, storage or rotor set", false);
+    if (bytes < H.bytes) return fail(b, LBM_ERR_INVALID_ARG, "state buffer too small", false);
+    if (H.step < 0 || (b->inplace && (H.step & 1)))
+        return fail(b, LBM_ERR_INVALID_ARG, "bad step in the state", false);
+    lbm_status s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    if ((H.step & 1) != (b->host_step & 1)) {
+        // keep every lattice's live state in array f[step & 1]
+        for (auto& In : b->inst) std::swap(In.h.f[0], In.h.f[1]);
+        b->dirty = true;
+    }
+    b->host_step = H.step;
+    s = sync_descriptors(b);
+    if (s != LBM_OK) return s;
+    const char* p = (const char*)buf + sizeof H;
+    for (auto& sec : state_sections(b, I)) {
+        CK(cudaMemcpyAsync(sec.dev, p, sec.bytes, cudaMemcpyHostToDevice, b->stream));
+        p += sec.bytes;
+    }
+    CK(write_step_slot(b));
+    return check_device_errors(b);
+}
+
+lbm_status lbm_set_wait_limit(lbm_ctx* ctx, long long cycles)
+{
+    ENTER(ctx);
+    if (cycles < 0) return fail(b, LBM_ERR_INVALID_ARG, "wait limit < 0", false);
+    b->wait_cycles = cycles;
+    drop_graphs(b);  // the captured launches hold the old bound
+    return LBM_OK;
 }
 
 // Staged rows need one-row tiles and every lattice's nx a multiple of the

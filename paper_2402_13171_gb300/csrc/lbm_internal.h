@@ -3,14 +3,18 @@
 // structs are copied to device memory as they are.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "lbm_gb300.h"
 
 namespace lbmgb {
 
 constexpr int kMaxTurbines = 16;    // rotors per lattice
 constexpr int kMaxElements = 4096;  // blade elements per lattice
 constexpr int kMaxInstances = 64;   // lattices per batch
+constexpr long long kDefaultWaitCycles = 1ll << 31;  // ~1 s of SM clock before a device wait is declared failed
 
 enum Bc : int { BC_PERIODIC = 0, BC_INOUT = 1, BC_NOSLIP = 2, BC_FREESLIP = 3 };
 enum Coll : int { COLL_CUMULANT = 0, COLL_SRT_SMAG = 1 };
@@ -96,6 +100,7 @@ struct StepArgs {
     int diag_every;                     // diagnostic period shared by the batch (0 = off)
     int tile_z;                         // planes per CTA (1: no marching); for the rotor launch the deepest rotor tile
     int staged;                         // rows staged in shared memory by persistent CTAs
+    long long wait_cycles;              // bound of the staged step's copy-barrier waits (SM clock cycles)
 };
 
 // Planes a rotor tile covers at most (consecutive z-blocks of its column are
@@ -114,6 +119,30 @@ __host__ __device__ inline unsigned long long pack_tile(int inst, int z, int y0,
 __host__ __device__ inline int tile_lattice(unsigned long long t) { return (int)((t >> 48) & 0xFF); }
 __host__ __device__ inline int tile_planes(unsigned long long t) { return (int)((t >> 56) & 0x7F) + 1; }
 
+// Host-side checks of a rotor description shared by alm_add_turbine and
+// alm_eval_static: blade and element counts in [1, max_elements] each and their
+// product at most max_elements (formed in 64 bits, so it cannot wrap), and every
+// real-valued input finite (a NaN hub would pass the support test, whose
+// comparisons are all false for NaN).
+inline bool turbine_counts_ok(const alm_turbine_desc* d, long long max_elements)
+{
+    if (d->n_blades < 1 || d->n_elements < 1 || d->n_blades > max_elements || d->n_elements > max_elements) return false;
+    return (long long)d->n_blades * (long long)d->n_elements <= max_elements;
+}
+inline bool turbine_values_finite(const alm_turbine_desc* d)
+{
+    const double v[] = {d->hub[0], d->hub[1], d->hub[2], d->radius, d->epsilon, d->omega, d->yaw, d->pitch,
+                        d->theta0, d->chord_root, d->chord_tip};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    if (d->twist)
+        for (int k = 0; k < d->n_elements; ++k)
+            if (!std::isfinite(d->twist[k])) return false;
+    for (int i = 0; i < d->n_polar; ++i)
+        if (!std::isfinite(d->alpha[i]) || !std::isfinite(d->cl[i]) || !std::isfinite(d->cd[i])) return false;
+    return true;
+}
+
 // Host-side launchers (lbm_kernels.cu).
 // rotor: the launch over the rotor tiles (element culling, force gather, the
 // actuator line of the next step) rather than over the rest.  dependent: a
@@ -127,13 +156,14 @@ cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStrea
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
 int staged_blocks_per_sm(int coll, int store, int width);
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);
-cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const float* drho,
-                        const float* u, const float* fneq, int parity, int inflow_mean, cudaStream_t s);
+cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const double* rho,
+                        const double* u, const float* fneq, int parity, int inflow_mean, cudaStream_t s);
 cudaError_t launch_moments(int store, const DevDomain* d_dom_inst, const DevDomain& h, int parity, double* rho,
                            double* u, cudaStream_t s);
 cudaError_t launch_probe(int store, const DevDomain* d_dom_inst, int parity, const long long* cells, int n, double* out,
                          cudaStream_t s);
-cudaError_t launch_to_float(int store, const void* src, float* dst, long long n, cudaStream_t s);
-cudaError_t launch_from_float(int store, const float* src, void* dst, long long n, cudaStream_t s);
+// One PDF plane of n values as FP64 populations w + h, and back.
+cudaError_t launch_plane_to_f64(int store, const void* src, double* dst, long long n, double w, cudaStream_t s);
+cudaError_t launch_plane_from_f64(int store, const double* src, void* dst, long long n, double w, cudaStream_t s);
 
 }  // namespace lbmgb

@@ -255,6 +255,87 @@ __device__ __forceinline__ void inv_k1(const Axis& a, float k1, float& fm, float
     f0 = -fm - fp;
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+
+// The f32x2 forms of add, sub, mul and fma (sm_100 and later): one instruction
+// on two FP32 lanes, each rounded exactly as the scalar instruction, so a
+// paired evaluation gives the scalar evaluation's bits in half the issue slots.
+#define LBM_F32X2(op)                                                                                        \
+    "{\n .reg .b64 x_, y_, r_;\n mov.b64 x_, {%2, %3};\n mov.b64 y_, {%4, %5};\n " op                    \
+    " r_, x_, y_;\n mov.b64 {%0, %1}, r_;\n}"
+__device__ __forceinline__ float2 add2(float2 x, float2 y)
+{
+    float2 r;
+    asm(LBM_F32X2("add.rn.f32x2") : "=f"(r.x), "=f"(r.y) : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2(float2 x, float2 y)
+{
+    float2 r;
+    asm(LBM_F32X2("sub.rn.f32x2") : "=f"(r.x), "=f"(r.y) : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2(float2 x, float2 y)
+{
+    float2 r;
+    asm(LBM_F32X2("mul.rn.f32x2") : "=f"(r.x), "=f"(r.y) : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));
+    return r;
+}
+#undef LBM_F32X2
+__device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z)
+{
+    float2 r;
+    asm("{\n .reg .b64 x_, y_, z_, r_;\n mov.b64 x_, {%2, %3};\n mov.b64 y_, {%4, %5};\n mov.b64 z_, {%6, %7};\n"
+        " fma.rn.f32x2 r_, x_, y_, z_;\n mov.b64 {%0, %1}, r_;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y), "f"(z.x), "f"(z.y));
+    return r;
+}
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+// Raw moments as raw_moments computes them (same operations, same order), with
+// the populations of the planes c_z = -1 and c_z = +1 carried as pairs:
+// hp[3j + i] = (h[3j + i], h[18 + 3j + i]), hs[3j + i] = h[9 + 3j + i].
+__device__ __forceinline__ Moments raw_moments_paired(const float2 hp[9], const float hs[9])
+{
+    float2 m0p[3], m1p[3], m2p[3];
+    float m0s[3], m1s[3], m2s[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        m2p[j] = add2(hp[3 * j + 2], hp[3 * j]);
+        m0p[j] = add2(m2p[j], hp[3 * j + 1]);
+        m1p[j] = sub2(hp[3 * j + 2], hp[3 * j]);
+        m2s[j] = hs[3 * j + 2] + hs[3 * j];
+        m0s[j] = m2s[j] + hs[3 * j + 1];
+        m1s[j] = hs[3 * j + 2] - hs[3 * j];
+    }
+    // per z level k: pairs hold levels 0 and 2, scalars level 1
+    const float2 A02p = add2(m0p[2], m0p[0]);
+    const float2 A00p = add2(A02p, m0p[1]);
+    const float2 A10p = add2(add2(m1p[0], m1p[1]), m1p[2]);
+    const float2 A20p = add2(add2(m2p[0], m2p[1]), m2p[2]);
+    const float2 A01p = sub2(m0p[2], m0p[0]);
+    const float2 A11p = sub2(m1p[2], m1p[0]);
+    const float A02s = m0s[2] + m0s[0];
+    const float A00s = A02s + m0s[1];
+    const float A10s = m1s[0] + m1s[1] + m1s[2];
+    const float A20s = m2s[0] + m2s[1] + m2s[2];
+    const float A01s = m0s[2] - m0s[0];
+    const float A11s = m1s[2] - m1s[0];
+    Moments M;
+    M.Szz = A00p.y + A00p.x;
+    M.drho = M.Szz + A00s;
+    M.jx = A10p.x + A10s + A10p.y;
+    M.jy = A01p.x + A01s + A01p.y;
+    M.jz = A00p.y - A00p.x;
+    M.Sxx = A20p.x + A20s + A20p.y;
+    M.Syy = A02p.x + A02s + A02p.y;
+    M.Sxy = A11p.x + A11s + A11p.y;
+    M.Sxz = A10p.y - A10p.x;
+    M.Syz = A01p.y - A01p.x;
+    return M;
+}
+
 // Cumulant collision with shear rate omega, bulk and all higher-order rates 1
 // (all cumulants above second order relax to zero, so post-collision central
 // moments of order 4 and 6 are the Gaussian products of the second-order ones,
@@ -272,10 +353,22 @@ __device__ __forceinline__ void inv_k1(const Axis& a, float k1, float& fm, float
 // Second-order indices are held halved
 // (moment (a, b, c) scaled by 2^-(number of indices equal to 2)), so that every
 // pass receives h2 = k2/2 directly.
+//
+// The values of the z levels c_z = -1 and +1 travel as FP32 pairs through all
+// three passes: the z pass produces them together (its f(-1), f(+1)), and the
+// y and x passes treat the two levels alike (their weights are even in c_z), so
+// those passes run on f32x2 instructions for two thirds of their columns.
 __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy, float Fz, float omega, float& drho_o,
                                                  float& jx_o, float& jy_o, float& jz_o)
 {
-    const Moments M = raw_moments(h);
+    float2 hp[9];
+    float hs[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        hp[r] = make_float2(h[r], h[18 + r]);
+        hs[r] = h[9 + r];
+    }
+    const Moments M = raw_moments_paired(hp, hs);
     const float rho = 1.0f + M.drho;
     // correctly rounded: the equilibrium momentum rho (j + F/2)/rho must not
     // carry a one-signed reciprocal error, or the lattice momentum drifts
@@ -323,48 +416,93 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
         d222 = (0.125f * rho) * g;
     }
     const Axis X = axis_of(ux), Y = axis_of(uy), Z = axis_of(uz);
-    // z pass over the columns (a, b); G[k][b][a], k the population index along z
-    float G[27];
-#define GZ(a, b) G[(b) * 3 + (a)], G[9 + (b) * 3 + (a)], G[18 + (b) * 3 + (a)]
-    inv_k1h2(Z, hFz, d002, GZ(0, 0));
-    inv_k0k1(Z, hFx, bxz, GZ(1, 0));
-    inv_k0h2(Z, d200, d202, GZ(2, 0));
-    inv_k0k1(Z, hFy, byz, GZ(0, 1));
-    inv_k0h2(Z, bxy, d112, GZ(1, 1));
-    inv_k1(Z, d211, GZ(2, 1));
-    inv_k0h2(Z, d020, d022, GZ(0, 2));
-    inv_k1(Z, d121, GZ(1, 2));
-    inv_k0h2(Z, d220, d222, GZ(2, 2));
-#undef GZ
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float dz = dphi(Z, k - 1);
-        const float gz = fmaf(M.drho, w1(k - 1) + dz, dz);  // rho phi_z - w1
-        G[k * 9 + 0] += gz;
-        G[k * 9 + 2] = fmaf(1.0f / 6.0f, gz, G[k * 9 + 2]);
-        G[k * 9 + 6] = fmaf(1.0f / 6.0f, gz, G[k * 9 + 6]);
-        G[k * 9 + 8] = fmaf(1.0f / 36.0f, gz, G[k * 9 + 8]);
+    // z pass over the columns (a, b): the pair (f(-1), f(+1)) = Gp[3b + a] and
+    // f(0) = Gs[3b + a]; the map's coefficients enter as pairs (dm, dp), (bm, bp)
+    const float2 zd = make_float2(Z.dm, Z.dp), zb = make_float2(Z.bm, Z.bp);
+    float2 Gp[9];
+    float Gs[9];
+    auto z_k1h2 = [&](int c, float k1, float h2) {
+        Gp[c] = fma2(zb, bc2(k1), bc2(h2));
+        Gs[c] = -Gp[c].x - Gp[c].y;
+    };
+    auto z_k0k1 = [&](int c, float k0, float k1) {
+        Gp[c] = fma2(zd, bc2(k0), mul2(zb, bc2(k1)));
+        Gs[c] = k0 - Gp[c].x - Gp[c].y;
+    };
+    auto z_k0h2 = [&](int c, float k0, float h2) {
+        Gp[c] = fma2(zd, bc2(k0), bc2(h2));
+        Gs[c] = k0 - Gp[c].x - Gp[c].y;
+    };
+    auto z_k1 = [&](int c, float k1) {
+        Gp[c] = mul2(zb, bc2(k1));
+        Gs[c] = -Gp[c].x - Gp[c].y;
+    };
+    z_k1h2(0, hFz, d002);
+    z_k0k1(1, hFx, bxz);
+    z_k0h2(2, d200, d202);
+    z_k0k1(3, hFy, byz);
+    z_k0h2(4, bxy, d112);
+    z_k1(5, d211);
+    z_k0h2(6, d020, d022);
+    z_k1(7, d121);
+    z_k0h2(8, d220, d222);
+    {
+        // equilibrium part of the z pass: rho phi_z - w1 on the columns (0, 0),
+        // (2, 0), (0, 2), (2, 2) with the weights 1, 1/6, 1/6, 1/36
+        const float2 gzp = fma2(bc2(M.drho), add2(bc2(w1(1)), zd), zd);  // w1(-1) = w1(+1)
+        Gp[0] = add2(Gp[0], gzp);
+        Gp[2] = fma2(bc2(1.0f / 6.0f), gzp, Gp[2]);
+        Gp[6] = fma2(bc2(1.0f / 6.0f), gzp, Gp[6]);
+        Gp[8] = fma2(bc2(1.0f / 36.0f), gzp, Gp[8]);
+        const float dz = -Z.u2;
+        const float gz = fmaf(M.drho, w1(0) + dz, dz);
+        Gs[0] += gz;
+        Gs[2] = fmaf(1.0f / 6.0f, gz, Gs[2]);
+        Gs[6] = fmaf(1.0f / 6.0f, gz, Gs[6]);
+        Gs[8] = fmaf(1.0f / 36.0f, gz, Gs[8]);
     }
     // y pass over the columns (a, k); the equilibrium part e0_a w1 dphi_y enters
     // as the moments (0, u_y, -u_y^2), which the map takes to dphi_y
+    const float2 ydm = bc2(Y.dm), ydp = bc2(Y.dp), ybm = bc2(Y.bm), ybp = bc2(Y.bp);
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float k1 = G[k * 9 + 3 + a], h2 = G[k * 9 + 6 + a];
-            if (a != 1) {
-                const float e = (a == 0 ? 1.0f : 1.0f / 6.0f) * w1(k - 1);
-                k1 = fmaf(e, uy, k1);
-                h2 = fmaf(-0.5f * e, Y.u2, h2);
-            }
-            inv_full(Y, G[k * 9 + a], k1, h2, G[k * 9 + a], G[k * 9 + 3 + a], G[k * 9 + 6 + a]);
+    for (int a = 0; a < 3; ++a) {
+        float2 k1p = Gp[3 + a], h2p = Gp[6 + a];
+        float k1s = Gs[3 + a], h2s = Gs[6 + a];
+        if (a != 1) {
+            const float ea = a == 0 ? 1.0f : 1.0f / 6.0f;
+            const float ep = ea * w1(1), es = ea * w1(0);  // w1(-1) = w1(+1)
+            k1p = fma2(bc2(ep), bc2(uy), k1p);
+            h2p = fma2(bc2(-0.5f * ep), bc2(Y.u2), h2p);
+            k1s = fmaf(es, uy, k1s);
+            h2s = fmaf(-0.5f * es, Y.u2, h2s);
         }
+        const float2 k0p = Gp[a];
+        const float2 fm = fma2(ydm, k0p, fma2(ybm, k1p, h2p));
+        const float2 fp = fma2(ydp, k0p, fma2(ybp, k1p, h2p));
+        Gp[a] = fm;
+        Gp[3 + a] = sub2(sub2(k0p, fm), fp);
+        Gp[6 + a] = fp;
+        inv_full(Y, Gs[a], k1s, h2s, Gs[a], Gs[3 + a], Gs[6 + a]);
+    }
     // x pass over the rows (j, k), with w1 w1 dphi_x entered the same way
+    const float2 xdm = bc2(X.dm), xdp = bc2(X.dp), xbm = bc2(X.bm), xbp = bc2(X.bp);
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-        const float e = w2(r % 3 - 1, r / 3 - 1);
-        const float k1 = fmaf(e, ux, G[3 * r + 1]), h2 = fmaf(-0.5f * e, X.u2, G[3 * r + 2]);
-        inv_full(X, G[3 * r], k1, h2, h[3 * r], h[3 * r + 1], h[3 * r + 2]);
+    for (int j = 0; j < 3; ++j) {
+        const float ep = w2(j - 1, 1), es = w2(j - 1, 0);  // w2(j, -1) = w2(j, +1)
+        const float2 k1p = fma2(bc2(ep), bc2(ux), Gp[3 * j + 1]);
+        const float2 h2p = fma2(bc2(-0.5f * ep), bc2(X.u2), Gp[3 * j + 2]);
+        const float2 k0p = Gp[3 * j];
+        const float2 fm = fma2(xdm, k0p, fma2(xbm, k1p, h2p));
+        const float2 fp = fma2(xdp, k0p, fma2(xbp, k1p, h2p));
+        const float2 f0 = sub2(sub2(k0p, fm), fp);
+        h[3 * j] = fm.x;
+        h[3 * j + 1] = f0.x;
+        h[3 * j + 2] = fp.x;
+        h[18 + 3 * j] = fm.y;
+        h[18 + 3 * j + 1] = f0.y;
+        h[18 + 3 * j + 2] = fp.y;
+        const float k1s = fmaf(es, ux, Gs[3 * j + 1]), h2s = fmaf(-0.5f * es, X.u2, Gs[3 * j + 2]);
+        inv_full(X, Gs[3 * j], k1s, h2s, h[9 + 3 * j], h[9 + 3 * j + 1], h[9 + 3 * j + 2]);
     }
     drho_o = M.drho;
     jx_o = M.jx + Fx;
@@ -1314,7 +1452,7 @@ __host__ __device__ inline size_t bulk_smem_bytes(int width, int elem_bytes)
 }
 
 constexpr int kMaxStages = 4;
-constexpr long long kWaitCycles = 1ll << 31;  // ~1 s of SM clock before a wait is declared failed
+constexpr long long kWaitCycles = kDefaultWaitCycles;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -1326,12 +1464,15 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase of the given parity; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+// Bounded wait for the phase of the given parity: tries until `limit` SM clock
+// cycles have passed, false if the phase did not complete by then (a limit of
+// 0 gives up before the first try).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit)
 {
     const unsigned a = smem_addr(bar);
     const long long t0 = clock64();
     for (;;) {
+        if (clock64() - t0 >= limit) return false;
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -1339,7 +1480,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
     }
 }
 // One row of bytes (16-byte aligned, multiple of 16) from global to shared memory,
@@ -1447,7 +1587,7 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
             ++issued;
         }
         const int sidx = (int)(k % S);
-        if (!mbar_wait(s_full + sidx, (k / S) & 1u)) {
+        if (!mbar_wait(s_full + sidx, (k / S) & 1u, A.wait_cycles)) {
             s_abort = 1;
             atomicOr(A.dom->err, ERR_TIMEOUT);
         }
@@ -1628,11 +1768,12 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
         }
     }
     // after a failed wait: the copies still in flight (segments k .. issued - 1)
-    // land before the CTA exits, each wait bounded again
+    // land before the CTA exits, each wait bounded again, by the full limit
+    // whatever the bound of the step's own waits
     if (s_abort) {
         __syncthreads();
         if (tid == 0)
-            for (unsigned j = k; j < issued; ++j) (void)mbar_wait(s_full + j % S, (j / S) & 1u);
+            for (unsigned j = k; j < issued; ++j) (void)mbar_wait(s_full + j % S, (j / S) & 1u, kWaitCycles);
         __syncthreads();
     }
     // diagnostic step: the last CTA closes the sums of every lattice
@@ -1679,10 +1820,11 @@ __global__ void k_inflow(const DevDomain* D, long long step)
     }
 }
 
-// f = feq(1 + drho, u) + fneq as offsets.  u = nullptr: the mean inflow profile
-// when inflow_mean, else 0.
+// f = feq(rho, u) + fneq as offsets, from device copies of the caller's FP64
+// rho and u (drho = rho - 1 and u rounded to FP32 here) and FP32 fneq.
+// u = nullptr: the mean inflow profile when inflow_mean, else 0.
 template <typename T>
-__global__ void k_init(const DevDomain* D, const float* drho, const float* u, const float* fneq, int parity,
+__global__ void k_init(const DevDomain* D, const double* rho, const double* u, const float* fneq, int parity,
                        int inflow_mean)
 {
     const long long N = D->N;
@@ -1690,9 +1832,9 @@ __global__ void k_init(const DevDomain* D, const float* drho, const float* u, co
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         float ux = 0.f, uy = 0.f, uz = 0.f;
         if (u) {
-            ux = u[i];
-            uy = u[N + i];
-            uz = u[2 * N + i];
+            ux = (float)u[i];
+            uy = (float)u[N + i];
+            uz = (float)u[2 * N + i];
         } else if (inflow_mean) {
             const int z = (int)(i / ((long long)D->nx * D->ny));
             double scale = 1.0;
@@ -1702,7 +1844,7 @@ __global__ void k_init(const DevDomain* D, const float* drho, const float* u, co
             uz = (float)(D->u_ref[2] * scale);
         }
         float E[27];
-        feq_offsets(drho ? drho[i] : 0.0f, ux, uy, uz, E);
+        feq_offsets(rho ? (float)(rho[i] - 1.0) : 0.0f, ux, uy, uz, E);
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             float v = E[q];
@@ -1761,18 +1903,20 @@ __global__ void k_probe(const DevDomain* D, int parity, const long long* cells, 
     }
 }
 
+// One PDF plane as absolute FP64 populations w + h (read-out, checkpoints) and back
+// (h = f - w rounded to FP32, then to the storage type).
 template <typename T>
-__global__ void k_to_float(const T* src, float* dst, long long n)
+__global__ void k_plane_to_f64(const T* src, double* dst, long long n, double w)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = Io<T>::ldcg(src + i);
+        dst[i] = w + (double)Io<T>::ldcg(src + i);
 }
 
 template <typename T>
-__global__ void k_from_float(const float* src, T* dst, long long n)
+__global__ void k_plane_from_f64(const double* src, T* dst, long long n, double w)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        Io<T>::st(dst + i, src[i]);
+        Io<T>::st(dst + i, (float)(src[i] - w));
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1890,13 +2034,13 @@ cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const float* drho, const float* u,
+cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const double* rho, const double* u,
                         const float* fneq, int parity, int inflow_mean, cudaStream_t s)
 {
     const int g = grid_for(h.N, 256);
-    if (store == STORE_FP32) k_init<float><<<g, 256, 0, s>>>(d_dom_inst, drho, u, fneq, parity, inflow_mean);
-    else if (store == STORE_BF16) k_init<__nv_bfloat16><<<g, 256, 0, s>>>(d_dom_inst, drho, u, fneq, parity, inflow_mean);
-    else k_init<__half><<<g, 256, 0, s>>>(d_dom_inst, drho, u, fneq, parity, inflow_mean);
+    if (store == STORE_FP32) k_init<float><<<g, 256, 0, s>>>(d_dom_inst, rho, u, fneq, parity, inflow_mean);
+    else if (store == STORE_BF16) k_init<__nv_bfloat16><<<g, 256, 0, s>>>(d_dom_inst, rho, u, fneq, parity, inflow_mean);
+    else k_init<__half><<<g, 256, 0, s>>>(d_dom_inst, rho, u, fneq, parity, inflow_mean);
     return cudaGetLastError();
 }
 
@@ -1920,21 +2064,21 @@ cudaError_t launch_probe(int store, const DevDomain* d_dom_inst, int parity, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_float(int store, const void* src, float* dst, long long n, cudaStream_t s)
+cudaError_t launch_plane_to_f64(int store, const void* src, double* dst, long long n, double w, cudaStream_t s)
 {
     const int g = grid_for(n, 256);
-    if (store == STORE_FP32) k_to_float<float><<<g, 256, 0, s>>>((const float*)src, dst, n);
-    else if (store == STORE_BF16) k_to_float<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16*)src, dst, n);
-    else k_to_float<__half><<<g, 256, 0, s>>>((const __half*)src, dst, n);
+    if (store == STORE_FP32) k_plane_to_f64<float><<<g, 256, 0, s>>>((const float*)src, dst, n, w);
+    else if (store == STORE_BF16) k_plane_to_f64<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16*)src, dst, n, w);
+    else k_plane_to_f64<__half><<<g, 256, 0, s>>>((const __half*)src, dst, n, w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_from_float(int store, const float* src, void* dst, long long n, cudaStream_t s)
+cudaError_t launch_plane_from_f64(int store, const double* src, void* dst, long long n, double w, cudaStream_t s)
 {
     const int g = grid_for(n, 256);
-    if (store == STORE_FP32) k_from_float<float><<<g, 256, 0, s>>>(src, (float*)dst, n);
-    else if (store == STORE_BF16) k_from_float<__nv_bfloat16><<<g, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n);
-    else k_from_float<__half><<<g, 256, 0, s>>>(src, (__half*)dst, n);
+    if (store == STORE_FP32) k_plane_from_f64<float><<<g, 256, 0, s>>>(src, (float*)dst, n, w);
+    else if (store == STORE_BF16) k_plane_from_f64<__nv_bfloat16><<<g, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n, w);
+    else k_plane_from_f64<__half><<<g, 256, 0, s>>>(src, (__half*)dst, n, w);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,9 @@
 //  - The first call on a device looks up the block's device address with
 //    cudaGetSymbolAddress, with that device current.  Make that first call
 //    before any stream capture.
+//  - The rotor descriptor and polar table reach the block by copies from
+//    pageable host memory (the call's own stack and a host vector), so the
+//    call may wait for earlier work on its stream before it returns.
 //  - All calls share the block and it keeps the last call's contents.  Calls
 //    that overlap on the GPU (different streams, or host threads without
 //    ordering) race on it; serialise them on one stream.
@@ -92,8 +95,8 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
     if (nx < 1 || ny < 1 || nz < 1 || nx > 65535 || ny > 65535 || nz > 65535) return LBM_ERR_INVALID_ARG;
     const long long N = (long long)nx * ny * nz;
     if (27LL * N >= (1LL << 31)) return LBM_ERR_INVALID_ARG;
+    if (!turbine_counts_ok(d, kStaticMaxElements)) return LBM_ERR_INVALID_ARG;
     const int n_el = d->n_blades * d->n_elements;
-    if (d->n_blades < 1 || d->n_elements < 1 || n_el > kStaticMaxElements) return LBM_ERR_INVALID_ARG;
     if (d->n_polar < 2 || d->n_polar > kStaticMaxPolar || !d->alpha || !d->cl || !d->cd) return LBM_ERR_INVALID_ARG;
     if (d->regularisation != ALM_REG_GAUSSIAN && d->regularisation != ALM_REG_ROMA) return LBM_ERR_INVALID_ARG;
     if (d->tip_loss != 0 && d->tip_loss != 1) return LBM_ERR_INVALID_ARG;
@@ -102,6 +105,9 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
     const double cut = roma ? 1.5 : 3.0 * d->epsilon;
     for (int i = 1; i < d->n_polar; ++i)
         if (!(d->alpha[i] > d->alpha[i - 1])) return LBM_ERR_INVALID_ARG;
+    if (!turbine_values_finite(d)) return LBM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (body_force && !std::isfinite(body_force[a])) return LBM_ERR_INVALID_ARG;
     const double cy = std::cos(d->yaw), sy = std::sin(d->yaw);
     const double ea[3] = {cy, sy, 0.0}, e1[3] = {-sy, cy, 0.0}, e2[3] = {0.0, 0.0, 1.0};
     const int n[3] = {nx, ny, nz};

@@ -120,6 +120,10 @@ def load():
                          ctypes.POINTER(ctypes.c_double)],
         "lbm_get_tile": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "lbm_get_state_size": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+        "lbm_get_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+        "lbm_set_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+        "lbm_set_wait_limit": [ctypes.c_void_p, ctypes.c_longlong],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -280,9 +284,18 @@ class Lattice:
     def sync(self):
         self._call("lbm_sync")
 
-    def moments(self):
-        rho = np.empty((self.nz, self.ny, self.nx))
-        u = np.empty((3, self.nz, self.ny, self.nx))
+    def moments(self, rho=None, u=None):
+        """rho (nz, ny, nx) and u (3, nz, ny, nx) as float64, into new arrays or
+        into the caller's (C-contiguous float64 arrays of N and 3N values, for
+        example views of page-locked memory, which the device copies into
+        directly)."""
+        if rho is None:
+            rho = np.empty((self.nz, self.ny, self.nx))
+        if u is None:
+            u = np.empty((3, self.nz, self.ny, self.nx))
+        for a, n in ((rho, self.N), (u, 3 * self.N)):
+            _require(a.dtype == np.float64 and a.flags.c_contiguous and a.size == n,
+                     "moment outputs must be C-contiguous float64 arrays of N and 3N values")
         self._call("lbm_get_moments", _p(rho), _p(u))
         return rho, u
 
@@ -305,6 +318,22 @@ class Lattice:
         a = np.ascontiguousarray(f, dtype=np.float64)
         _require(a.size == 27 * self.N, "PDFs need 27*nx*ny*nz values")
         self._call("lbm_set_pdfs", _p(a))
+
+    def state(self):
+        """Checkpoint blob (numpy uint8 array) for a bitwise resume with set_state."""
+        n = ctypes.c_size_t()
+        self._call("lbm_get_state_size", ctypes.byref(n))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._call("lbm_get_state", ctypes.c_void_p(buf.ctypes.data), n)
+        return buf
+
+    def set_state(self, buf):
+        a = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._call("lbm_set_state", ctypes.c_void_p(a.ctypes.data), ctypes.c_size_t(a.size))
+
+    def set_wait_limit(self, cycles):
+        """Bound of the staged step's copy-barrier waits (SM clock cycles)."""
+        self._call("lbm_set_wait_limit", ctypes.c_longlong(int(cycles)))
 
     def loads(self, tid=0, elements=False):
         th = ctypes.c_double()

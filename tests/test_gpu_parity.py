@@ -381,7 +381,73 @@ def test_loads_sink_matches_synchronous_reads():
     gs.destroy()
 
 
-def test_checkpoint_resume_is_bitwise():
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_checkpoint_resume_is_bitwise(storage):
+    """A lattice with a rotor, inlet noise and diagnostics, checkpointed after
+    11 steps (lbm_get_state) and restored into a lattice with another history:
+    at step 17 PDFs, rotor loads, element forces and diagnostics are bit for
+    bit those of the uninterrupted run."""
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True, storage=storage, diag_every=4)
+    ga.step(11)
+    blob = ga.state()
+    ga.step(6)
+    gb, _ = setup_pair(dom, [turb], inflow=True, storage=storage, diag_every=4)
+    gb.step(3)          # different history, then restore
+    gb.set_state(blob)
+    assert gb.step_count() == 11
+    gb.step(6)
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    tha, tqa, efa, epa = ga.loads(0, elements=True)
+    thb, tqb, efb, epb = gb.loads(0, elements=True)
+    assert (tha, tqa) == (thb, tqb)
+    np.testing.assert_array_equal(efa, efb)
+    np.testing.assert_array_equal(epa, epb)
+    assert ga.diagnostics()[1] == gb.diagnostics()[1] == 16
+    np.testing.assert_array_equal(ga.diagnostics()[0], gb.diagnostics()[0])
+    # a state of another lattice shape or rotor set is refused
+    gc = gpu_lattice(dict(dom, nx=dom["nx"] + 8))
+    from paper_2402_13171_gb300 import lbm
+    with pytest.raises(lbm.LbmError, match="invalid argument"):
+        gc.set_state(blob)
+    gc.destroy()
+
+
+def test_checkpoint_resume_at_odd_step_and_in_a_batch():
+    """The state taken at an odd step restores into a lattice at an even step
+    (the live array changes side), and a batch member restores from a state
+    taken alone."""
+    from paper_2402_13171_gb300 import lbm
+    dom, turb = small_rotor_case()
+    ga, _ = setup_pair(dom, [turb], inflow=True)
+    ga.step(7)
+    blob = ga.state()
+    ga.step(5)
+    d2 = dict(nx=33, ny=17, nz=9, nu=0.02, body_force=(1e-5, 0, 0))
+    cfgs = [dict(nx=dom["nx"], ny=dom["ny"], nz=dom["nz"], nu=dom["nu"], bc=dom["bc"], seed=dom["seed"]),
+            dict(nx=33, ny=17, nz=9, nu=0.02, body_force=(1e-5, 0, 0))]
+    lat = lbm.batch_create(cfgs)
+    lat[0].set_inflow(u_ref=dom["u_ref"], noise_rel=dom["noise_rel"])
+    lat[0].add_turbine(**turb)
+    rho, u, fneq = I.random_state(33, 17, 9, seed=3)
+    lat[1].init_fields(rho, u, fneq)
+    g1, _ = setup_pair(d2, rho=rho, u=u, fneq=fneq)
+    g1.step(7)
+    lat[0].step(2)
+    lat[1].set_state(g1.state())       # both members now at step 7
+    lat[0].set_state(blob)
+    lat[0].step(5)
+    g1.step(5)
+    np.testing.assert_array_equal(lat[0].pdfs(), ga.pdfs())
+    assert lat[0].loads(0) == ga.loads(0)
+    np.testing.assert_array_equal(lat[1].pdfs(), g1.pdfs())
+
+
+def test_pdf_restore_without_force_box_stays_close():
+    """lbm_set_pdfs + lbm_set_step restore the populations and step but not
+    the lagged rotor force, so a rotor run resumed that way departs from the
+    original by a small amount near the rotor; a lattice without rotors
+    resumes bit for bit."""
     dom, turb = small_rotor_case()
     ga, _ = setup_pair(dom, [turb], inflow=True)
     ga.step(11)
@@ -393,8 +459,6 @@ def test_checkpoint_resume_is_bitwise():
     gb.set_pdfs(f)
     gb.set_step(n)
     gb.step(6)
-    # the lagged ALM force is not part of the PDFs: compare flow away from the rotor box
-    # and the loads after the restart transient
     fa, fb = ga.pdfs(), gb.pdfs()
     assert np.abs(fa - fb).max() < 1e-4
     dom2 = dict(nx=20, ny=10, nz=6, nu=0.02, bc=("inout", "periodic", "periodic"), u_ref=(0.04, 0, 0),
@@ -424,19 +488,56 @@ def test_probe_matches_moments():
 
 
 def test_diagnostics_fp64_sums():
+    """The fused FP64 sums equal the sums of the lattice's own PDFs (mass as
+    the sum of the offsets f - w)."""
     dom = dict(nx=33, ny=17, nz=9, nu=0.02, body_force=(1e-5, 0, 0))
     rho, u, fneq = I.random_state(33, 17, 9, seed=3)
     g, s = setup_pair(dom, rho=rho, u=u, fneq=fneq, diag_every=5)
     g.step(11)  # diagnostic steps 0, 5, 10
     mm, at = g.diagnostics()
     assert at == 10
-    g2, _ = setup_pair(dom, rho=rho, u=u, fneq=fneq)
-    g2.step(11)
-    f = g2.pdfs()
-    C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
+    f = g.pdfs()
     # sums of the offsets: mass - N, momentum
     assert mm[0] == pytest.approx((f.sum() - f[0].size), abs=1e-6)
-    np.testing.assert_allclose(mm[1:], np.einsum("qa,qzyx->a", C, f), atol=1e-6)
+    np.testing.assert_allclose(mm[1:], np.einsum("qa,qzyx->a", C27, f), atol=1e-6)
+
+
+C27 = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], dtype=np.float64)
+
+
+@pytest.mark.parametrize("case", ["periodic_body_force", "rotor_inlet_outlet", "log_law_farm"])
+def test_diagnostics_match_oracle(case):
+    """The fused FP64 mass and momentum of the last diagnostic step against the
+    oracle's state after the same steps: a periodic lattice with a body force
+    (mass conserved, momentum grows by F per cell and step), the rotor case
+    with inlet noise and outlet, and the log-law farm with free-slip walls
+    (neither conserves momentum).  Tolerance: each cell's offsets stay within
+    the 2e-7 PDF parity bound, whose errors do not share a sign, so the sums
+    over N cells stay within 27 * 2e-7 * sqrt(N) (2e-3 at N = 1e5)."""
+    if case == "periodic_body_force":
+        dom = dict(nx=33, ny=17, nz=9, nu=0.02, body_force=(1e-5, 0, -3e-6))
+        rho, u, fneq = I.random_state(33, 17, 9, seed=3)
+        g, s = setup_pair(dom, rho=rho, u=u, fneq=fneq, diag_every=5)
+    elif case == "rotor_inlet_outlet":
+        dom, turb = small_rotor_case()
+        g, s = setup_pair(dom, [turb], inflow=True, diag_every=5)
+    else:
+        dom, turbs = I.small_farm_case(nx=64, ny=32, nz=28, diameter=8.0, elements_per_blade=4, x_hubs=(14.0, 40.0))
+        g, s = setup_pair(dom, turbs, inflow=True, diag_every=5)
+    g.step(11)
+    s.step(11)
+    mm, at = g.diagnostics()
+    assert at == 10
+    N = s.f[0].size
+    mass_o = s.f.sum() - N
+    mom_o = np.einsum("qa,qzyx->a", C27, s.f)
+    tol = 27 * 2e-7 * math.sqrt(N)
+    assert mm[0] == pytest.approx(mass_o, abs=tol)
+    np.testing.assert_allclose(mm[1:], mom_o, rtol=0, atol=tol)
+    if case == "periodic_body_force":
+        assert mm[0] == pytest.approx(s.f.sum() - N, abs=1e-6 * N ** 0.5)
+    else:
+        assert abs(mom_o[0]) > 10 * tol   # momentum carried by the inflow: the check is not vacuous
 
 
 def test_batch_equals_separate_runs():
@@ -488,3 +589,54 @@ def test_sixteen_bit_storage_tracks_fp32(storage):
     print(f"{storage}: max|du| vs oracle {err:.3e}, fp32 {np.abs(u32 - uo).max():.3e}")
     # 8-bit (bf16) / 11-bit (fp16) mantissas on offsets of ~0.05: per-step rounding 2e-4 / 2.5e-5
     assert err < (1e-3 if storage == "bf16" else 1e-4)
+
+
+def _rotor_checks(g, s, turbs, tag):
+    du = max_du(g, s)
+    print(f"{tag} step {s.step_count}: max|du| {du:.2e}")
+    assert du <= DU_TOL
+    off = 0
+    for t_i, t in enumerate(turbs):
+        ne = t["n_blades"] * t["n_elements"]
+        th, tq, ef, ep = g.loads(t_i, elements=True)
+        np.testing.assert_allclose(ep, s.elem_pos[off:off + ne], atol=2e-5)
+        fo = s.elem_force[off:off + ne]
+        np.testing.assert_allclose(ef, fo, atol=1e-7 + 5e-5 * np.abs(fo).max())
+        assert th == pytest.approx(s.loads[t_i, 0], rel=5e-5)
+        assert tq == pytest.approx(s.loads[t_i, 1], rel=5e-5)
+        off += ne
+
+
+@pytest.mark.parametrize("coll,kernel", [("cumulant", "gauss"), ("srt_smag", "gauss"), ("cumulant", "roma")])
+def test_yawed_twisted_pitched_rotor_on_unequal_polars(coll, kernel):
+    """A rotor yawed by 7 degrees, with a twist table, a collective pitch and a
+    start angle, on polars tabulated at unequal angles (the table search of the
+    non-uniform branch): flow, element positions and forces and FP64 loads
+    stay with the oracle over 50 steps."""
+    dom, turb = I.yawed_twisted_rotor(kernel=kernel)
+    dom["collision"] = coll
+    g, s = setup_pair(dom, [turb], inflow=True)
+    for n in (1, 10, 50):
+        g.step(n - s.step_count)
+        s.step(n - s.step_count)
+        _rotor_checks(g, s, [turb], f"yawed {coll}/{kernel}")
+
+
+def test_log_law_farm_two_yawed_rotors():
+    """A scaled-down farm: log-law inflow with noise, free-slip bottom and top,
+    periodic y, zero-gradient outlet and two yawed rotors in a row, the second
+    in the wake of the first.  The initial state is the log profile on both
+    sides; one step matches PDF for PDF, then the flow and every rotor's loads
+    stay with the oracle over 40 steps."""
+    dom, turbs = I.small_farm_case()
+    g, s = setup_pair(dom, turbs, inflow=True)
+    _, u0 = g.moments()
+    prof = I.log_law_profile(dom["nz"], dom["u_ref"][0], dom["z0"], dom["z_ref"])
+    np.testing.assert_allclose(u0[0, :, 5, 5], prof, atol=1e-8)
+    g.step(1)
+    s.step(1)
+    np.testing.assert_allclose(g.pdfs(), s.f, atol=F_TOL, rtol=0)
+    for n in (10, 40):
+        g.step(n - s.step_count)
+        s.step(n - s.step_count)
+        _rotor_checks(g, s, turbs, "log-law farm")

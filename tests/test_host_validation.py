@@ -79,11 +79,19 @@ def _static_desc(**over):
 @pytest.mark.parametrize("over", [dict(regularisation=2), dict(regularisation=-1),
                                   dict(tip_loss=2), dict(tip_loss=-1),
                                   dict(epsilon=0.0), dict(epsilon=6.0), dict(radius=0.0),
-                                  dict(hub=(16.0, 10.9, 20.0), regularisation=1)])
+                                  dict(hub=(16.0, 10.9, 20.0), regularisation=1),
+                                  # 3 x 1431655766 wraps to 2 in 32-bit arithmetic
+                                  dict(n_blades=3, n_elements=1431655766), dict(n_blades=1025, n_elements=1),
+                                  dict(hub=(float("nan"), 20.0, 20.0)), dict(yaw=float("nan")),
+                                  dict(omega=float("inf")), dict(theta0=float("nan")), dict(pitch=float("-inf")),
+                                  dict(chord_tip=float("nan"))])
 def test_static_alm_rejects_bad_rotors_on_the_host(over):
     """alm_eval_static checks its rotor before any CUDA call: an unknown
-    regularisation or tip-loss code, a Gaussian width outside [0.5, 5], a zero radius, or
-    a Roma support (hub +- (R + 3/2 + 1)) that leaves [1, n-2]."""
+    regularisation or tip-loss code, a Gaussian width outside [0.5, 5], a zero radius,
+    a Roma support (hub +- (R + 3/2 + 1)) that leaves [1, n-2], blade and element
+    counts whose product exceeds the static limit (also where the 32-bit product
+    would wrap), and non-finite inputs (a NaN hub passes the support test, whose
+    comparisons are all false for NaN)."""
     L = lbm.load()
     fn = L.alm_eval_static
     fn.restype = ctypes.c_int
@@ -118,3 +126,21 @@ def test_inplace_flag_must_be_boolean():
     cfg.inplace = 2
     h = ctypes.c_void_p()
     assert L.lbm_create(ctypes.byref(cfg), ctypes.byref(h)) == INVALID_ARG
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("over", [dict(n_blades=3, n_elements=1431655766), dict(hub=(float("nan"), 20.0, 20.0)),
+                                  dict(yaw=float("nan")), dict(omega=float("nan"))])
+def test_add_turbine_rejects_wrapping_counts_and_non_finite_inputs(over):
+    """alm_add_turbine applies the same count and finiteness checks (the GPU
+    is needed only to create the lattice the rotor is added to)."""
+    L = lbm.load()
+    g = lbm.Lattice.create(64, 40, 40)
+    hub = over.pop("hub", None)
+    d, keep = _static_desc(**over)
+    if hub is not None:
+        for a in range(3):
+            d.hub[a] = hub[a]
+    tid = ctypes.c_int()
+    assert L.alm_add_turbine(g._h, ctypes.byref(d), ctypes.byref(tid)) == INVALID_ARG
+    g.destroy()
