@@ -206,8 +206,9 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const double* f);
  * the storage type, each rotor's lagged force box (the ALM force of the last
  * collision, which the next sampling of Sec. 2.2 reads), the actuator-line
  * element buffers and FP64 rotor loads of both step parities, the inlet
- * velocity columns of both parities, the last diagnostic sums -- and the
- * step counter, behind a header with the lattice's shape.  The blob is
+ * ghost populations (the equilibria the x = 0 cells pull) of both parities,
+ * the last diagnostic sums -- and the step counter, behind a header with the
+ * lattice's shape.  The blob is
  * host memory owned by the caller: lbm_get_state_size gives its size,
  * lbm_get_state fills it, lbm_set_state restores it into a lattice of the
  * same sizes, storage, collision, boundary rules and rotors (INVALID_ARG

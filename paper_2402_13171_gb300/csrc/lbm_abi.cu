@@ -240,14 +240,14 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
         CK(cudaMemcpyAsync(h.inflow_scale, ones.data(), sizeof(float) * c.nz, cudaMemcpyHostToDevice, b->stream));
         if (b->stream) CK(cudaStreamSynchronize(b->stream));
     }
-    h.inflow_u[0] = h.inflow_u[1] = nullptr;
+    h.inflow_ghost[0] = h.inflow_ghost[1] = nullptr;
     if (c.bc[0] == LBM_BC_INFLOW_OUTFLOW) {
-        const size_t ib = sizeof(float) * 3 * (size_t)c.ny * c.nz;
-        float* u2 = (float*)dalloc(b, 2 * ib);
-        if (!u2) return fail(b, LBM_ERR_OOM, "inflow buffer allocation failed");
-        CK(cudaMemsetAsync(u2, 0, 2 * ib, b->stream));
-        h.inflow_u[0] = u2;
-        h.inflow_u[1] = u2 + 3 * (size_t)c.ny * c.nz;
+        const size_t ib = sizeof(float) * 9 * (size_t)c.ny * c.nz;
+        float* g2 = (float*)dalloc(b, 2 * ib);
+        if (!g2) return fail(b, LBM_ERR_OOM, "inflow buffer allocation failed");
+        CK(cudaMemsetAsync(g2, 0, 2 * ib, b->stream));
+        h.inflow_ghost[0] = g2;
+        h.inflow_ghost[1] = g2 + 9 * (size_t)c.ny * c.nz;
     }
     const size_t fbytes = (size_t)h.N * 27 * store_bytes(b->store);
     for (int p = 0; p < (c.inplace ? 1 : 2); ++p) {
@@ -390,6 +390,10 @@ StepArgs step_args(Batch* b, int parity)
     a.tile_z = b->tile_z;
     a.staged = b->staged;
     a.wait_cycles = b->wait_cycles;
+    a.walls = 0;
+    for (auto& I : b->inst)
+        for (int ax = 0; ax < 3; ++ax)
+            if (I.h.bc[ax] == BC_NOSLIP || I.h.bc[ax] == BC_FREESLIP) a.walls = 1;
     return a;
 }
 
@@ -433,7 +437,25 @@ lbm_status launch_one(Batch* b, int parity)
     ab.tiles = b->d_tiles + R;
     ab.n_tiles = Nb;
     if (R > 0) CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));
-    if (Nb > 0) CK(launch_step(b->coll, b->store, dim3(Nb), block, b->stream, ab, false, R > 0));
+    if (Nb > 0) {
+        BulkParams bp{};
+        for (size_t i = 0; i < b->inst.size(); ++i) {
+            const DevDomain& h = b->inst[i].h;
+            LatHot& L = bp.lat[i];
+            L.nx = h.nx;
+            L.ny = h.ny;
+            L.nz = h.nz;
+            L.N = (unsigned)h.N;
+            L.inout = h.bc[0] == BC_INOUT ? 1 : 0;
+            L.omega = h.omega;
+            L.tau0 = h.tau0;
+            L.smag_c2 = h.smag_c2;
+            for (int a3 = 0; a3 < 3; ++a3) L.body[a3] = h.body[a3];
+            L.f[0] = h.f[0];
+            L.f[1] = h.f[1];
+        }
+        CK(launch_step(b->coll, b->store, dim3(Nb), block, b->stream, ab, false, R > 0, &bp));
+    }
     return LBM_OK;
 }
 
@@ -1104,7 +1126,7 @@ struct Section {
 
 // The device state one step reads and writes, beyond the descriptors: the
 // PDFs of the current step, each rotor's lagged force box, the actuator-line
-// element buffers and rotor loads of both step parities, the inlet columns of
+// element buffers and rotor loads of both step parities, the inlet ghost columns of
 // both parities, and the last diagnostic sums.
 std::vector<Section> state_sections(Batch* b, Instance& I)
 {
@@ -1119,8 +1141,8 @@ std::vector<Section> state_sections(Batch* b, Instance& I)
         }
     if (h.n_turb > 0)
         for (int p = 0; p < 2; ++p) v.push_back({h.loads[p], sizeof(double) * 2 * h.n_turb});
-    if (h.inflow_u[0])
-        for (int p = 0; p < 2; ++p) v.push_back({h.inflow_u[p], sizeof(float) * 3 * (size_t)h.ny * h.nz});
+    if (h.inflow_ghost[0])
+        for (int p = 0; p < 2; ++p) v.push_back({h.inflow_ghost[p], sizeof(float) * 9 * (size_t)h.ny * h.nz});
     v.push_back({h.diag_res, sizeof(double) * 5});
     return v;
 }

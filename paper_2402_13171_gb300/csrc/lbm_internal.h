@@ -65,7 +65,9 @@ struct DevDomain {
     unsigned long long seed;
     float u_ref_f[3], noise_amp_f;
     float* inflow_scale;       // nz: mean-profile factor per z plane (1, or the log law)
-    float* inflow_u[2];        // by step parity: inlet velocity per column, [3][nz][ny] (x inlet only)
+    float* inflow_ghost[2];    // by step parity: inlet ghost populations per column (x inlet only):
+                               // [9][nz][ny] offsets feq_q(1, u_in) - w_q of the nine directions with
+                               // c_x = +1, index (cz + 1) * 3 + (cy + 1)
     void* f[2];                // PDF offset arrays [27][nz][ny][nx] of the storage type
     int n_turb;
     DevTurbine* turb;          // device array of n_turb
@@ -101,6 +103,21 @@ struct StepArgs {
     int tile_z;                         // planes per CTA (1: no marching); for the rotor launch the deepest rotor tile
     int staged;                         // rows staged in shared memory by persistent CTAs
     long long wait_cycles;              // bound of the staged step's copy-barrier waits (SM clock cycles)
+    int walls;                          // some lattice has a no-slip or free-slip face
+};
+
+// Per-lattice values the bulk launch reads for every cell, passed in its
+// kernel parameters (constant bank) rather than read from the descriptor.
+struct LatHot {
+    int nx, ny, nz;
+    unsigned N;
+    int inout;                 // x inlet/outlet (else periodic x)
+    float omega, tau0, smag_c2;
+    float body[3];
+    void* f[2];
+};
+struct BulkParams {
+    LatHot lat[kMaxInstances];
 };
 
 // Planes a rotor tile covers at most (consecutive z-blocks of its column are
@@ -148,8 +165,10 @@ inline bool turbine_values_finite(const alm_turbine_desc* d)
 // actuator line of the next step) rather than over the rest.  dependent: a
 // bulk launch that directly follows its own step's rotor launch on the stream
 // and may overlap it (programmatic stream serialization).
+// bulk: the lattices' per-cell parameters for the bulk kernel of lattices
+// without wall faces (nullptr: the general kernel).
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
-                        bool dependent);
+                        bool dependent, const BulkParams* bulk = nullptr);
 // The in-place (AA) step over the whole work list: odd steps read and write a
 // cell's own slots, even steps pull and push across neighbours.
 cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd);

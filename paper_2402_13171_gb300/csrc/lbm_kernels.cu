@@ -155,6 +155,22 @@ __device__ __forceinline__ float feq_offset_one(int q, float ux, float uy, float
     return dx[i] * py[j] * pz[k] + w1(i - 1) * (dy[j] * pz[k] + w1(j - 1) * dz[k]);
 }
 
+// Inlet ghost populations of column (y, z) for step `step`: the offsets
+// feq_q(rho = 1, u_in) - w_q of the nine directions with c_x = +1 (the values
+// the x = 0 cells pull across the inlet face from that column), written once
+// per column and step instead of once per pulling cell and direction.
+__device__ __forceinline__ void write_inlet_ghost(const DevDomain* D, long long step, int y, int z)
+{
+    float u[3];
+    inflow_velocity(D, step, y, z, u);
+    float* g = D->inflow_ghost[step & 1];
+    const int plane = D->ny * D->nz, col = z * D->ny + y;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) g[(k * 3 + j) * plane + col] = feq_offset_one(k * 9 + j * 3 + 2, u[0], u[1], u[2]);
+}
+
 // ------------------------------------------------------------------ moments
 
 struct Moments {
@@ -599,10 +615,9 @@ __device__ __noinline__ void boundary_patch(const DevDomain* D, const T* src, in
         for (int a = 0; a < 3; ++a)
             if (D->bc[a] == BC_PERIODIC) s[a] = s[a] < 0 ? s[a] + n[a] : (s[a] >= n[a] ? s[a] - n[a] : s[a]);
         if (D->bc[0] == BC_INOUT) {
-            if (s[0] < 0) {
-                const float* ub = D->inflow_u[step & 1];
-                const int plane = D->ny * D->nz, col = s[2] * D->ny + s[1];
-                h[q] = feq_offset_one(qm, ub[col], ub[plane + col], ub[2 * plane + col]);
+            if (s[0] < 0) {  // the mirrored direction still has c_x = +1: a ghost population
+                const float* gb = D->inflow_ghost[step & 1];
+                h[q] = gb[((cm[2] + 1) * 3 + (cm[1] + 1)) * (D->ny * D->nz) + s[2] * D->ny + s[1]];
                 continue;
             }
             if (s[0] >= n[0]) s[0] = n[0] - 1;
@@ -893,8 +908,9 @@ __device__ __forceinline__ unsigned long long ld_tile(const unsigned long long* 
 }
 
 // Pulled pre-collision populations of cell (x, y, z): clamped/wrapped loads,
-// then the inlet and wall rules.
-template <typename T>
+// then the inlet and wall rules (WALLS false: the lattices have no no-slip or
+// free-slip face, and the wall code is left out).
+template <typename T, bool WALLS = true>
 __device__ __forceinline__ void load_cell(const DevDomain* D, const T* __restrict__ src, int x, int y, int z,
                                           long long step, float h[27])
 {
@@ -909,9 +925,9 @@ __device__ __forceinline__ void load_cell(const DevDomain* D, const T* __restric
     else { ym = max(ym, 0); yp = min(yp, ny - 1); }
     if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
     else { zm = max(zm, 0); zp = min(zp, nz - 1); }
-    const bool walls = ((bx == BC_NOSLIP || bx == BC_FREESLIP) && (x == 0 || x == nx - 1)) ||
-                       ((by == BC_NOSLIP || by == BC_FREESLIP) && (y == 0 || y == ny - 1)) ||
-                       ((bz == BC_NOSLIP || bz == BC_FREESLIP) && (z == 0 || z == nz - 1));
+    const bool walls = WALLS && (((bx == BC_NOSLIP || bx == BC_FREESLIP) && (x == 0 || x == nx - 1)) ||
+                                 ((by == BC_NOSLIP || by == BC_FREESLIP) && (y == 0 || y == ny - 1)) ||
+                                 ((bz == BC_NOSLIP || bz == BC_FREESLIP) && (z == 0 || z == nz - 1)));
     // 32-bit offsets: 27 N < 2^31 is checked on the host
     const unsigned uN = (unsigned)D->N;
     const unsigned xs[3] = {(unsigned)xp, (unsigned)x, (unsigned)xm};  // source x for cx = -1, 0, +1
@@ -929,24 +945,22 @@ __device__ __forceinline__ void load_cell(const DevDomain* D, const T* __restric
             }
         }
     // x inlet: the nine directions with c_x = +1 come from the ghost column
-    // (y - c_y, z - c_z): equilibrium at rho = 1 and that column's inlet velocity
+    // (y - c_y, z - c_z): equilibrium at rho = 1 and that column's inlet velocity,
+    // precomputed per column in the ghost buffer
     if (bx == BC_INOUT && x == 0) {
-        const float* ub = D->inflow_u[step & 1];
+        const float* gb = D->inflow_ghost[step & 1];
         const int plane = ny * nz;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const int q = k * 9 + j * 3 + 2;
-                const bool wall = (by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
-                                  (bz == BC_NOSLIP && ((k == 2 && z == 0) || (k == 0 && z == nz - 1)));
-                if (!wall) {
-                    const int col = (int)zs[k] * ny + (int)ys[j];
-                    h[q] = feq_offset_one(q, ub[col], ub[plane + col], ub[2 * plane + col]);
-                }
+                const bool wall = WALLS && ((by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
+                                            (bz == BC_NOSLIP && ((k == 2 && z == 0) || (k == 0 && z == nz - 1))));
+                if (!wall) h[q] = gb[(k * 3 + j) * plane + (int)zs[k] * ny + (int)ys[j]];
             }
     }
-    if (walls) {
+    if (WALLS && walls) {
         float hl[27];
 #pragma unroll
         for (int q = 0; q < 27; ++q) hl[q] = h[q];
@@ -1089,15 +1103,7 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
 #pragma unroll
             for (int q = 0; q < 27; ++q) h[q] = hn[q];
             if (MARCH && z + 1 < z1) load_cell<T>(D, src, x, y, z + 1, step, hn);
-            if (D->bc[0] == BC_INOUT && x == 0) {
-                float u[3];
-                inflow_velocity(D, step + 1, y, z, u);
-                float* ub = D->inflow_u[(step + 1) & 1];
-                const int plane = ny * nz, col = z * ny + y;
-                ub[col] = u[0];
-                ub[plane + col] = u[1];
-                ub[2 * plane + col] = u[2];
-            }
+            if (D->bc[0] == BC_INOUT && x == 0) write_inlet_ghost(D, step + 1, y, z);
             float F[3] = {D->body[0], D->body[1], D->body[2]};
             rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
             float m, jx, jy, jz;
@@ -1195,7 +1201,7 @@ __device__ __forceinline__ void diag_close(const StepArgs& A, const DevDomain* D
 // single-plane cumulant bulk, whose collision fits them without spills, so 8
 // CTAs of 128 threads (32 warps) are resident per SM; 85 for the rotor tiles
 // and the Smagorinsky collision; 128 for marching, which holds two planes.
-template <int COLL, typename T, bool MARCH, bool ROTOR>
+template <int COLL, typename T, bool MARCH, bool ROTOR, bool WALLS = true>
 __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMULANT) ? 3 : 4)) k_step(const StepArgs A)
 {
     if (ROTOR) asm volatile("griddepcontrol.launch_dependents;");
@@ -1240,23 +1246,15 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
             const T* __restrict__ src = (const T*)D->f[A.parity];
             T* __restrict__ dst = (T*)D->f[A.parity ^ 1];
             float hn[27];
-            load_cell<T>(D, src, x, y, z0, step, hn);
+            load_cell<T, WALLS>(D, src, x, y, z0, step, hn);
 #pragma unroll 1
             for (int z = z0; z < z1; ++z) {
                 float h[27];
 #pragma unroll
                 for (int q = 0; q < 27; ++q) h[q] = hn[q];
-                if (MARCH && z + 1 < z1) load_cell<T>(D, src, x, y, z + 1, step, hn);
-                // the x = 0 lane of each row prepares the inlet velocity of its column for step n+1
-                if (D->bc[0] == BC_INOUT && x == 0) {
-                    float u[3];
-                    inflow_velocity(D, step + 1, y, z, u);
-                    float* ub = D->inflow_u[(step + 1) & 1];
-                    const int plane = ny * nz, col = z * ny + y;
-                    ub[col] = u[0];
-                    ub[plane + col] = u[1];
-                    ub[2 * plane + col] = u[2];
-                }
+                if (MARCH && z + 1 < z1) load_cell<T, WALLS>(D, src, x, y, z + 1, step, hn);
+                // the x = 0 lane of each row prepares the inlet ghost populations of its column for step n+1
+                if (D->bc[0] == BC_INOUT && x == 0) write_inlet_ghost(D, step + 1, y, z);
                 float m, jx, jy, jz;
                 if (COLL == COLL_CUMULANT)
                     collide_cumulant(h, D->body[0], D->body[1], D->body[2], D->omega, m, jx, jy, jz);
@@ -1279,6 +1277,85 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
     if constexpr (!ROTOR) {
         if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     }
+}
+
+// The bulk launch for lattices without no-slip or free-slip faces (y and z
+// then periodic, x periodic or inlet/outlet), which is almost every cell of
+// the workloads: the same update as k_step's bulk path, with the lattice's
+// sizes, rates and array pointers read from the kernel parameters instead of
+// its descriptor in global memory, and no wall code compiled in.  Inlet cells
+// take their nine ghost populations from the inlet buffer.
+template <int COLL, typename T>
+__global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_bulk(const StepArgs A, const BulkParams P)
+{
+    __shared__ double s_red[8][4];
+    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
+    const int inst = tile_lattice(tile);
+    const LatHot& L = P.lat[inst];
+    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
+    const int x = (int)(tile & 0xFFFF) + threadIdx.x;
+    const long long step = __ldcg(A.step_slot + A.parity);
+    if (A.write_step && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        A.step_slot[A.parity ^ 1] = step + 1;
+        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
+    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;  // uniform over the grid
+    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    if (x < nx && y < ny) {
+        const T* __restrict__ src = (const T*)L.f[A.parity];
+        T* __restrict__ dst = (T*)L.f[A.parity ^ 1];
+        const unsigned uN = L.N;
+        int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+        if (L.inout) { xm = max(xm, 0); xp = min(xp, nx - 1); }  // outlet: zero-gradient clamp
+        else { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
+        if (ym < 0) ym += ny; if (yp >= ny) yp -= ny;
+        if (zm < 0) zm += nz; if (zp >= nz) zp -= nz;
+        const unsigned xs[3] = {(unsigned)xp, (unsigned)x, (unsigned)xm};
+        const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+        const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+        float h[27];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const unsigned row = (zs[k] * (unsigned)ny + ys[j]) * (unsigned)nx;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int q = k * 9 + j * 3 + i;
+                    h[q] = Io<T>::ld(src + ((unsigned)q * uN + row + xs[i]));
+                }
+            }
+        if (L.inout && x == 0) {
+            // the nine directions with c_x = +1 across the inlet face, from the ghost
+            // columns (y - c_y, z - c_z); then this column's ghosts for step n+1
+            const DevDomain* D = A.dom + inst;
+            const float* gb = D->inflow_ghost[step & 1];
+            const int plane = ny * nz;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) h[k * 9 + j * 3 + 2] = gb[(k * 3 + j) * plane + (int)zs[k] * ny + (int)ys[j]];
+            write_inlet_ghost(D, step + 1, y, z);
+        }
+        float m, jx, jy, jz;
+        if (COLL == COLL_CUMULANT)
+            collide_cumulant(h, L.body[0], L.body[1], L.body[2], L.omega, m, jx, jy, jz);
+        else
+            collide_srt_smag(h, L.body[0], L.body[1], L.body[2], L.tau0, L.smag_c2, m, jx, jy, jz);
+        if (diag) {
+            o_m = m;
+            o_jx = jx;
+            o_jy = jy;
+            o_jz = jz;
+        }
+        const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
+    }
+    if (diag) diag_close(A, A.dom + inst, step, o_m, o_jx, o_jy, o_jz, s_red);
+    if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ in-place (AA) step
@@ -1682,7 +1759,7 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
                 if (bz == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
                 else { zm = max(zm, 0); zp = min(zp, nz - 1); }
                 const int ys3[3] = {yp, y, ym}, zs3[3] = {zp, z, zm};
-                const float* ub = D->inflow_u[step & 1];
+                const float* gb = D->inflow_ghost[step & 1];
                 const int plane = ny * nz;
 #pragma unroll
                 for (int kk = 0; kk < 3; ++kk)
@@ -1691,10 +1768,7 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
                         const int q = kk * 9 + j * 3 + 2;
                         const bool wall = (by == BC_NOSLIP && ((j == 2 && y == 0) || (j == 0 && y == ny - 1))) ||
                                           (bz == BC_NOSLIP && ((kk == 2 && z == 0) || (kk == 0 && z == nz - 1)));
-                        if (!wall) {
-                            const int col = zs3[kk] * ny + ys3[j];
-                            h[q] = feq_offset_one(q, ub[col], ub[plane + col], ub[2 * plane + col]);
-                        }
+                        if (!wall) h[q] = gb[(kk * 3 + j) * plane + zs3[kk] * ny + ys3[j]];
                     }
             }
             const bool walls = ((bx == BC_NOSLIP || bx == BC_FREESLIP) && (x == 0 || x == nx - 1)) ||
@@ -1708,15 +1782,7 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
 #pragma unroll
                 for (int q = 0; q < 27; ++q) h[q] = hl[q];
             }
-            if (bx == BC_INOUT && x == 0) {
-                float u[3];
-                inflow_velocity(D, step + 1, y, z, u);
-                float* ub = D->inflow_u[(step + 1) & 1];
-                const int plane = ny * nz, col = z * ny + y;
-                ub[col] = u[0];
-                ub[plane + col] = u[1];
-                ub[2 * plane + col] = u[2];
-            }
+            if (bx == BC_INOUT && x == 0) write_inlet_ghost(D, step + 1, y, z);
             float F[3] = {D->body[0], D->body[1], D->body[2]};
             if (rotor_tile) rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
             float m, jx, jy, jz;
@@ -1806,18 +1872,12 @@ __global__ void k_alm(const DevDomain* dom, int parity, long long step)
     if (D->n_el > 0) alm_compute<T>(D, (const T*)D->f[parity], step);
 }
 
-// Inlet velocities of every column for step `step` (after a state change).
+// Inlet ghost populations of every column for step `step` (after a state change).
 __global__ void k_inflow(const DevDomain* D, long long step)
 {
     const int plane = D->ny * D->nz;
-    float* ub = D->inflow_u[step & 1];
-    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < plane; col += gridDim.x * blockDim.x) {
-        float u[3];
-        inflow_velocity(D, step, col % D->ny, col / D->ny, u);
-        ub[col] = u[0];
-        ub[plane + col] = u[1];
-        ub[2 * plane + col] = u[2];
-    }
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < plane; col += gridDim.x * blockDim.x)
+        write_inlet_ghost(D, step, col % D->ny, col / D->ny);
 }
 
 // f = feq(rho, u) + fneq as offsets, from device copies of the caller's FP64
@@ -1965,8 +2025,24 @@ cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStrea
     return cudaErrorInvalidValue;
 }
 
+static cudaError_t launch_dependent_bulk(void (*kernel)(StepArgs, BulkParams), dim3 grid, dim3 block, cudaStream_t s,
+                                         const StepArgs& a, const BulkParams& p)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a, p);
+}
+
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
-                        bool dependent)
+                        bool dependent, const BulkParams* bulk)
 {
     const bool march = a.tile_z > 1;
 #define LBM_STEP_CASE(C, S, T)                                                                        \
@@ -1978,10 +2054,14 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
             if (rotor) k_step<C, T, true, true><<<grid, block, 0, s>>>(a);                            \
             else if (dependent) return launch_dependent(k_step<C, T, true, false>, grid, block, s, a);  \
             else k_step<C, T, true, false><<<grid, block, 0, s>>>(a);                                 \
+        } else if (rotor) {                                                                           \
+            k_step<C, T, false, true><<<grid, block, 0, s>>>(a);                                      \
+        } else if (a.walls || !bulk) {                                                                \
+            if (dependent) return launch_dependent(k_step<C, T, false, false>, grid, block, s, a);    \
+            k_step<C, T, false, false><<<grid, block, 0, s>>>(a);                                     \
         } else {                                                                                      \
-            if (rotor) k_step<C, T, false, true><<<grid, block, 0, s>>>(a);                           \
-            else if (dependent) return launch_dependent(k_step<C, T, false, false>, grid, block, s, a); \
-            else k_step<C, T, false, false><<<grid, block, 0, s>>>(a);                                \
+            if (dependent) return launch_dependent_bulk(k_bulk<C, T>, grid, block, s, a, *bulk);      \
+            k_bulk<C, T><<<grid, block, 0, s>>>(a, *bulk);                                            \
         }                                                                                             \
         return cudaGetLastError();                                                                    \
     }
