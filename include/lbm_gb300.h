@@ -94,10 +94,12 @@ typedef struct {
                                 0 = direct loads */
     int inplace;             /* 1: one PDF array updated in place (AA pattern: even steps pull from the
                                 neighbours and push into the slots they read, odd steps read and write a
-                                cell's own slots), half the PDF memory.  Needs periodic or no-slip faces,
-                                no rotor, single-plane direct tiles; the state read-out and write calls
-                                (moments, probe, PDFs, init, inflow, step counter) need an even step
-                                count, where the array equals the two-array scheme's.  0 = two arrays */
+                                cell's own slots), half the PDF memory, for every boundary rule and
+                                rotors (the outlet keeps a copy of its last plane, 9 ny nz values per
+                                step parity).  Needs single-plane direct tiles; the state read-out and
+                                write calls (moments, probe, PDFs, state, init, inflow, step counter,
+                                autotune) need an even step count, where the array equals the two-array
+                                scheme's.  0 = two arrays */
 } lbm_config;
 
 typedef struct {

@@ -197,11 +197,6 @@ lbm_status validate_cfg(const lbm_config* c, std::string& msg)
     }
     if (c->inplace != 0 && c->inplace != 1) { msg = "inplace must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
     if (c->inplace) {
-        for (int a = 0; a < 3; ++a)
-            if (c->bc[a] != LBM_BC_PERIODIC && c->bc[a] != LBM_BC_NOSLIP) {
-                msg = "the in-place scheme takes periodic and no-slip faces only";
-                return LBM_ERR_UNSUPPORTED;
-            }
         if (tz != 1 || c->staged) {
             msg = "the in-place scheme takes single-plane direct tiles only";
             return LBM_ERR_UNSUPPORTED;
@@ -248,6 +243,15 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
         CK(cudaMemsetAsync(g2, 0, 2 * ib, b->stream));
         h.inflow_ghost[0] = g2;
         h.inflow_ghost[1] = g2 + 9 * (size_t)c.ny * c.nz;
+    }
+    h.outlet[0] = h.outlet[1] = nullptr;
+    if (c.inplace && c.bc[0] == LBM_BC_INFLOW_OUTFLOW) {
+        const size_t ob = sizeof(float) * 9 * (size_t)c.ny * c.nz;
+        float* o2 = (float*)dalloc(b, 2 * ob);
+        if (!o2) return fail(b, LBM_ERR_OOM, "outlet buffer allocation failed");
+        CK(cudaMemsetAsync(o2, 0, 2 * ob, b->stream));
+        h.outlet[0] = o2;
+        h.outlet[1] = o2 + 9 * (size_t)c.ny * c.nz;
     }
     const size_t fbytes = (size_t)h.N * 27 * store_bytes(b->store);
     for (int p = 0; p < (c.inplace ? 1 : 2); ++p) {
@@ -411,19 +415,14 @@ cudaError_t write_step_slot(Batch* b)
 }
 
 // One time step.  Staged rows: one persistent launch over the whole work list.
-// Otherwise two launches of k_step: the rotor tiles (first in the list), then
-// the rest, allowed to overlap the rotor launch; the step counter is advanced
-// by the second (or by the only one).
-lbm_status launch_one(Batch* b, int parity)
+// Otherwise two launches (k_step or, in place, k_step_aa): the rotor tiles
+// (first in the list), then the rest, allowed to overlap the rotor launch;
+// the step counter is advanced by the second (or by the only one).
+// diag_step: the step is a diagnostic step (never inside a captured graph).
+lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
 {
     const StepArgs a = step_args(b, parity);
     const dim3 block(b->tile_x, b->tile_y);
-    if (b->inplace) {
-        StepArgs aa = a;
-        aa.write_step = 1;
-        CK(launch_step_aa(b->coll, b->store, dim3(b->n_tiles), block, b->stream, aa, parity == 1));
-        return LBM_OK;
-    }
     if (b->staged) {
         CK(launch_step(b->coll, b->store, dim3(std::min(b->n_tiles, b->staged_grid)), block, b->stream, a, false,
                        false));
@@ -436,6 +435,11 @@ lbm_status launch_one(Batch* b, int parity)
     ar.tile_z = b->rotor_planes;  // > 1: the marching rotor kernel, each tile over its own planes
     ab.tiles = b->d_tiles + R;
     ab.n_tiles = Nb;
+    if (b->inplace) {
+        if (R > 0) CK(launch_step_aa(b->coll, b->store, dim3(R), block, b->stream, ar, parity == 1, true, false));
+        if (Nb > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nb), block, b->stream, ab, parity == 1, false, R > 0));
+        return LBM_OK;
+    }
     if (R > 0) CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));
     if (Nb > 0) {
         BulkParams bp{};
@@ -454,7 +458,7 @@ lbm_status launch_one(Batch* b, int parity)
             L.f[0] = h.f[0];
             L.f[1] = h.f[1];
         }
-        CK(launch_step(b->coll, b->store, dim3(Nb), block, b->stream, ab, false, R > 0, &bp));
+        CK(launch_step(b->coll, b->store, dim3(Nb), block, b->stream, ab, false, R > 0, &bp, diag_step));
     }
     return LBM_OK;
 }
@@ -465,8 +469,11 @@ lbm_status refresh_alm(Batch* b)
 {
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
-    for (size_t i = 0; i < b->inst.size(); ++i)
+    for (size_t i = 0; i < b->inst.size(); ++i) {
         if (b->inst[i].h.bc[0] == BC_INOUT) CK(launch_inflow(b->d_dom + i, b->inst[i].h, b->host_step, b->stream));
+        if (b->inst[i].h.outlet[0])
+            CK(launch_outlet_fill(b->store, b->d_dom + i, b->inst[i].h, b->host_step, b->stream));
+    }
     bool any = false;
     for (auto& I : b->inst) any = any || I.h.n_el > 0;
     if (!any) return LBM_OK;
@@ -694,7 +701,6 @@ lbm_status alm_add_turbine(lbm_ctx* ctx, const alm_turbine_desc* d, int* id_out)
 {
     ENTER(ctx);
     if (!d) return fail(b, LBM_ERR_INVALID_ARG, "null turbine", false);
-    if (b->inplace) return fail(b, LBM_ERR_UNSUPPORTED, "the in-place scheme takes no rotor", false);
     if ((int)I.turb.size() >= kMaxTurbines) return fail(b, LBM_ERR_INVALID_ARG, "too many rotors", false);
     if (!turbine_counts_ok(d, kMaxElements) || I.h.n_el + d->n_blades * d->n_elements > kMaxElements)
         return fail(b, LBM_ERR_INVALID_ARG, "element count out of range", false);
@@ -837,11 +843,21 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
     }
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
-    int left = n_steps;
-    if (b->profiling) {
-        // events bracket each graph replay (eight or two steps) or a single
-        // step, so timing does not break up the replays
-        while (left > 0) {
+    long long left = n_steps;
+    while (left > 0) {
+        const int p = (int)(b->host_step & 1);
+        // graphs (8 or 2 steps) cover no diagnostic step: those are single launches
+        long long room = left;
+        if (b->diag_every > 0) room = std::min(room, (b->diag_every - b->host_step % b->diag_every) % b->diag_every);
+        const int len = room >= kGraphSteps[1] ? 1 : (room >= kGraphSteps[0] ? 0 : -1);
+        const int k = (b->stream && len >= 0) ? kGraphSteps[len] : 1;
+        if (k > 1) {
+            s = ensure_graph(b, len, p);
+            if (s != LBM_OK) return s;
+        }
+        if (b->profiling) {
+            // events bracket each graph replay or single step, so timing does
+            // not break up the replays
             if (b->ev_used + 2 > b->ev.size()) {
                 if (b->ev.size() < 32768) {
                     cudaEvent_t e0, e1;
@@ -855,43 +871,21 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps)
                     if (s != LBM_OK) return s;
                 }
             }
-            const int p = (int)(b->host_step & 1);
-            const int len = left >= kGraphSteps[1] ? 1 : 0;
-            const int k = (b->stream && left >= 2) ? kGraphSteps[len] : 1;
-            if (k > 1) {
-                s = ensure_graph(b, len, p);
-                if (s != LBM_OK) return s;
-            }
             CK(cudaEventRecord(b->ev[b->ev_used], b->stream));
-            if (k > 1) {
-                CK(cudaGraphLaunch(b->gexec[len][p], b->stream));
-            } else {
-                s = launch_one(b, p);
-                if (s != LBM_OK) return s;
-            }
+        }
+        if (k > 1) {
+            CK(cudaGraphLaunch(b->gexec[len][p], b->stream));
+        } else {
+            s = launch_one(b, p, b->diag_every > 0 && b->host_step % b->diag_every == 0);
+            if (s != LBM_OK) return s;
+        }
+        if (b->profiling) {
             CK(cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
             b->ev_launches[b->ev_used / 2] = k;
             b->ev_used += 2;
-            b->host_step += k;
-            left -= k;
         }
-        return LBM_OK;
-    }
-    for (int len = 1; b->stream && len >= 0; --len) {
-        const int p = (int)(b->host_step & 1);
-        if (left < kGraphSteps[len]) continue;
-        s = ensure_graph(b, len, p);
-        if (s != LBM_OK) return s;
-        while (left >= kGraphSteps[len]) {
-            CK(cudaGraphLaunch(b->gexec[len][p], b->stream));
-            left -= kGraphSteps[len];
-            b->host_step += kGraphSteps[len];
-        }
-    }
-    for (; left > 0; --left) {
-        s = launch_one(b, (int)(b->host_step & 1));
-        if (s != LBM_OK) return s;
-        b->host_step++;
+        b->host_step += k;
+        left -= k;
     }
     return LBM_OK;
 }
@@ -1143,6 +1137,8 @@ std::vector<Section> state_sections(Batch* b, Instance& I)
         for (int p = 0; p < 2; ++p) v.push_back({h.loads[p], sizeof(double) * 2 * h.n_turb});
     if (h.inflow_ghost[0])
         for (int p = 0; p < 2; ++p) v.push_back({h.inflow_ghost[p], sizeof(float) * 9 * (size_t)h.ny * h.nz});
+    if (h.outlet[0])
+        for (int p = 0; p < 2; ++p) v.push_back({h.outlet[p], sizeof(float) * 9 * (size_t)h.ny * h.nz});
     v.push_back({h.diag_res, sizeof(double) * 5});
     return v;
 }
@@ -1360,6 +1356,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
 {
     NvtxRange nvtx_("lbm_autotune");
     ENTER(ctx);
+    REQUIRE_EVEN_STEP();
     if (steps_per_candidate < 1) return fail(b, LBM_ERR_INVALID_ARG, "steps_per_candidate < 1", false);
     const std::string key = tune_key(b);
     if (cache_path) {
@@ -1480,7 +1477,7 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
     // the same split as launch_one
-    *launches = (b->staged || b->inplace) ? 1 : (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
+    *launches = b->staged ? 1 : (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
     return LBM_OK;
 }
 

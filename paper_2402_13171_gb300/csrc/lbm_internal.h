@@ -68,6 +68,9 @@ struct DevDomain {
     float* inflow_ghost[2];    // by step parity: inlet ghost populations per column (x inlet only):
                                // [9][nz][ny] offsets feq_q(1, u_in) - w_q of the nine directions with
                                // c_x = +1, index (cz + 1) * 3 + (cy + 1)
+    float* outlet[2];          // by step parity (in-place lattices with an x outlet only): the last plane's
+                               // post-collision populations of the nine directions with c_x = -1,
+                               // [9][nz][ny], index (cz + 1) * 3 + (cy + 1)
     void* f[2];                // PDF offset arrays [27][nz][ny][nx] of the storage type
     int n_turb;
     DevTurbine* turb;          // device array of n_turb
@@ -166,12 +169,19 @@ inline bool turbine_values_finite(const alm_turbine_desc* d)
 // bulk launch that directly follows its own step's rotor launch on the stream
 // and may overlap it (programmatic stream serialization).
 // bulk: the lattices' per-cell parameters for the bulk kernel of lattices
-// without wall faces (nullptr: the general kernel).
+// without wall faces (nullptr: the general kernel); diag_step: the step is a
+// diagnostic step (the bulk kernel then carries the FP64 sums; the general
+// kernels read the step's diagnostic flag on the device).
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
-                        bool dependent, const BulkParams* bulk = nullptr);
+                        bool dependent, const BulkParams* bulk = nullptr, bool diag_step = false);
 // The in-place (AA) step over the whole work list: odd steps read and write a
 // cell's own slots, even steps pull and push across neighbours.
-cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd);
+// rotor / dependent as for launch_step.
+cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd,
+                           bool rotor, bool dependent);
+// Outlet copies of an in-place lattice for step `step`, from its current state.
+cudaError_t launch_outlet_fill(int store, const DevDomain* d_dom_inst, const DevDomain& h, long long step,
+                               cudaStream_t s);
 cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
 int staged_blocks_per_sm(int coll, int store, int width);
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);

@@ -45,6 +45,7 @@ template <> struct Io<float> {
     static __device__ __forceinline__ float ldw(const float* p) { return *p; }
     static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ float round(float v) { return v; }
 };
 // 16-bit loads ask L2 for the surrounding 256 bytes: a warp's 64-byte row
 // segment is a quarter of that, and the rest is the same row of the next
@@ -60,6 +61,7 @@ template <> struct Io<__nv_bfloat16> {
     static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
     static __device__ __forceinline__ float ldw(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 template <> struct Io<__half> {
     static __device__ __forceinline__ float ld(const __half* p)
@@ -71,6 +73,7 @@ template <> struct Io<__half> {
     static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
     static __device__ __forceinline__ float ldw(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
 };
 
 __device__ __forceinline__ float to_float(float v) { return v; }
@@ -552,15 +555,26 @@ __device__ __forceinline__ void collide_srt_smag(float h[27], float Fx, float Fy
     const float src = 1.0f - 0.5f * om;
     const float uu = ux * ux + uy * uy + uz * uz;
     const float uF = ux * Fx + uy * Fy + uz * Fz;
+    // h* = (1 - om) h + om feq + S, evaluated for each pair q, qbar = 26 - q
+    // together: c.u and c.F change sign with c, so om feq + S splits into a part
+    // even in c, w (om (drho + rho (4.5 (c.u)^2 - 1.5 u^2)) + src (9 (c.u)(c.F) - 3 u.F)),
+    // and an odd part, w 3 (om rho c.u + src c.F)
+    const float a = 1.0f - om;
+    const float om_rho = om * rho;
+    const float k1 = 4.5f * om_rho;
+    const float s9 = 9.0f * src;
+    const float k0 = fmaf(-1.5f * om_rho, uu, fmaf(om, M.drho, -3.0f * src * uF));
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
+    for (int q = 0; q < 13; ++q) {
         const float cx = (float)qcx(q), cy = (float)qcy(q), cz = (float)qcz(q);
         const float cu = cx * ux + cy * uy + cz * uz;
         const float cF = cx * Fx + cy * Fy + cz * Fz;
-        const float feq = wq(q) * (M.drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-        const float S = src * wq(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);
-        h[q] = h[q] - om * (h[q] - feq) + S;
+        const float pe = wq(q) * fmaf(cu, fmaf(k1, cu, s9 * cF), k0);
+        const float po = (3.0f * wq(q)) * fmaf(om_rho, cu, src * cF);
+        h[q] = fmaf(a, h[q], pe + po);
+        h[26 - q] = fmaf(a, h[26 - q], pe - po);
     }
+    h[13] = fmaf(a, h[13], wq(13) * k0);
     drho_o = M.drho;
     jx_o = M.jx + Fx;
     jy_o = M.jy + Fy;
@@ -755,7 +769,7 @@ __device__ __forceinline__ float tip_loss_factor(int n_blades, float R, float r,
 //  phase 3, warp 0: per-rotor FP64 sums in a fixed order (also written to the
 //    host loads sink when one is set).
 template <typename T>
-__device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long long step)
+__device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long long step, int swapped = 0)
 {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
@@ -776,10 +790,18 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
         }
         float4 out = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
         if (inside) {
+            // pulled populations of the corner cell: the pull sources, or (in-place
+            // array after an even step) the cell's own opposite slots
             float h[27];
+            if (swapped) {
+                const long long cc = cell_of(D, c[0], c[1], c[2]);
 #pragma unroll
-            for (int q = 0; q < 27; ++q)
-                h[q] = Io<T>::ldcg(f + (size_t)q * N + cell_of(D, c[0] - qcx(q), c[1] - qcy(q), c[2] - qcz(q)));
+                for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldcg(f + (size_t)(26 - q) * N + cc);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 27; ++q)
+                    h[q] = Io<T>::ldcg(f + (size_t)q * N + cell_of(D, c[0] - qcx(q), c[1] - qcy(q), c[2] - qcz(q)));
+            }
             float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
@@ -1026,6 +1048,54 @@ __device__ __forceinline__ void rotor_force(const DevDomain* D, long long step, 
     }
 }
 
+// Cull the blade elements whose support reaches the tile (planes [z0, z1)) into
+// shared memory, in element order; returns their number, or -1 when more than
+// KCULL reach it (every cell then scans all elements).  CTA-wide.
+template <int KCULL>
+__device__ __forceinline__ int cull_rotor_elements(const DevDomain* D, unsigned long long tile, long long step, int z0,
+                                                   int z1, float4* s_pos, float4* s_frc, int* s_tag, int* s_cnt)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    const float tx0 = (float)(tile & 0xFFFF), ty0 = (float)((tile >> 16) & 0xFFFF);
+    const float tx1 = tx0 + (float)(blockDim.x - 1), ty1 = ty0 + (float)(blockDim.y - 1);
+    const float tz0 = (float)z0, tz1 = (float)(z1 - 1);
+    const float4* P = D->el_pos[step & 1];
+    const float4* Fe = D->el_force[step & 1];
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
+    int total = 0;
+    for (int base = 0; base < D->n_el; base += nthreads) {
+        const int e = base + tid;
+        bool keep = false;
+        float4 pe = make_float4(0.f, 0.f, 0.f, 0.f);
+        int t = 0;
+        if (e < D->n_el) {
+            pe = __ldg(P + e);
+            while (t + 1 < D->n_turb && D->turb[t + 1].el_offset <= e) ++t;
+            const float cut = D->turb[t].cut;
+            keep = pe.x + cut >= tx0 && pe.x - cut <= tx1 && pe.y + cut >= ty0 && pe.y - cut <= ty1 &&
+                   pe.z + cut >= tz0 && pe.z - cut <= tz1;
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+        if (lane == 0) s_cnt[warp] = __popc(m);
+        __syncthreads();
+        int off = total, chunk = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            if (w < warp) off += s_cnt[w];
+            chunk += s_cnt[w];
+        }
+        const int pos = off + __popc(m & ((1u << lane) - 1u));
+        if (keep && pos < KCULL) {
+            s_pos[pos] = pe;
+            s_frc[pos] = __ldg(Fe + e);
+            s_tag[pos] = t;
+        }
+        total += chunk;
+        __syncthreads();
+    }
+    return total <= KCULL ? total : -1;
+}
+
 // The update of one rotor tile: cull the blade elements whose support reaches
 // the tile into shared memory (in element order; when more than KCULL reach it
 // every cell scans all elements), then each cell as in the bulk path plus the
@@ -1049,46 +1119,7 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
     const T* __restrict__ src = (const T*)D->f[parity];
     T* __restrict__ dst = (T*)D->f[parity ^ 1];
 
-    int n_cull;
-    {
-        const float tx0 = (float)(tile & 0xFFFF), ty0 = (float)((tile >> 16) & 0xFFFF);
-        const float tx1 = tx0 + (float)(blockDim.x - 1), ty1 = ty0 + (float)(blockDim.y - 1);
-        const float tz0 = (float)z0, tz1 = (float)(z1 - 1);
-        const float4* P = D->el_pos[step & 1];
-        const float4* Fe = D->el_force[step & 1];
-        const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
-        int total = 0;
-        for (int base = 0; base < D->n_el; base += nthreads) {
-            const int e = base + tid;
-            bool keep = false;
-            float4 pe = make_float4(0.f, 0.f, 0.f, 0.f);
-            int t = 0;
-            if (e < D->n_el) {
-                pe = __ldg(P + e);
-                while (t + 1 < D->n_turb && D->turb[t + 1].el_offset <= e) ++t;
-                const float cut = D->turb[t].cut;
-                keep = pe.x + cut >= tx0 && pe.x - cut <= tx1 && pe.y + cut >= ty0 && pe.y - cut <= ty1 &&
-                       pe.z + cut >= tz0 && pe.z - cut <= tz1;
-            }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-            if (lane == 0) s_cnt[warp] = __popc(m);
-            __syncthreads();
-            int off = total, chunk = 0;
-            for (int w = 0; w < nwarps; ++w) {
-                if (w < warp) off += s_cnt[w];
-                chunk += s_cnt[w];
-            }
-            const int pos = off + __popc(m & ((1u << lane) - 1u));
-            if (keep && pos < KCULL) {
-                s_pos[pos] = pe;
-                s_frc[pos] = __ldg(Fe + e);
-                s_tag[pos] = t;
-            }
-            total += chunk;
-            __syncthreads();
-        }
-        n_cull = total <= KCULL ? total : -1;
-    }
+    const int n_cull = cull_rotor_elements<KCULL>(D, tile, step, z0, z1, s_pos, s_frc, s_tag, s_cnt);
 
     // diagnostic partial sums of the thread's planes (diagnostic steps only),
     // in FP64 when it marches over several planes
@@ -1284,13 +1315,16 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
 // the workloads: the same update as k_step's bulk path, with the lattice's
 // sizes, rates and array pointers read from the kernel parameters instead of
 // its descriptor in global memory, and no wall code compiled in.  Inlet cells
-// take their nine ghost populations from the inlet buffer.
-template <int COLL, typename T>
-__global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_bulk(const StepArgs A, const BulkParams P)
+// take their nine ghost populations from the inlet buffer.  DIAG: the host
+// launches this form on diagnostic steps only (the sums' code costs the other
+// steps even when it does not run); SINGLE: one lattice, whose parameters are
+// then read at fixed offsets.
+template <int COLL, typename T, bool DIAG, bool SINGLE>
+__global__ void __launch_bounds__(256, 4) k_bulk(const StepArgs A, const BulkParams P)
 {
-    __shared__ double s_red[8][4];
+    __shared__ double s_red[DIAG ? 8 : 1][4];
     const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
-    const int inst = tile_lattice(tile);
+    const int inst = SINGLE ? 0 : tile_lattice(tile);
     const LatHot& L = P.lat[inst];
     const int z = (int)((tile >> 32) & 0xFFFF);
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
@@ -1300,7 +1334,6 @@ __global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_bulk(con
         A.step_slot[A.parity ^ 1] = step + 1;
         A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
     }
-    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;  // uniform over the grid
     float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     if (x < nx && y < ny) {
@@ -1344,7 +1377,7 @@ __global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_bulk(con
             collide_cumulant(h, L.body[0], L.body[1], L.body[2], L.omega, m, jx, jy, jz);
         else
             collide_srt_smag(h, L.body[0], L.body[1], L.body[2], L.tau0, L.smag_c2, m, jx, jy, jz);
-        if (diag) {
+        if (DIAG) {
             o_m = m;
             o_jx = jx;
             o_jy = jy;
@@ -1354,161 +1387,340 @@ __global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_bulk(con
 #pragma unroll
         for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
     }
-    if (diag) diag_close(A, A.dom + inst, step, o_m, o_jx, o_jy, o_jz, s_red);
+    if (DIAG) diag_close(A, A.dom + inst, step, o_m, o_jx, o_jy, o_jz, s_red);
     if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ in-place (AA) step
 
-// Offset of the slot cell (x, y, z) reads for direction q on an even in-place
-// step: the pull source A[q][x - c_q], wrapped on periodic axes, or
-// A[qbar][x] when the source lies past a no-slip wall (bounce-back).  The cell
-// writes its post-collision f*_q to the slot it read for qbar: A[qbar][x + c_q],
-// or its own free slot A[q][x] when x + c_q lies past a wall.
-__device__ __forceinline__ unsigned aa_even_offset(const DevDomain* D, int q, int x, int y, int z)
+// The in-place scheme keeps one PDF array A.  Before every even step it holds
+// the pull scheme's state, A[q][x] = f*_q(x) of the last collision.  A step
+// reads for each cell and direction q one "source" and, on even steps, writes
+// the post-collision f*_q into the source it read for the opposite direction
+// qbar; odd steps read A[qbar][x] and write A[q][x].  A source is the slot the
+// pull rules of load_cell / boundary_patch name (the pull source, the
+// cell's own opposite slot at a no-slip face, the mirrored slot at a free-slip
+// face), or a value no slot holds: an inlet ghost population, or at the
+// outlet the zero-gradient copy of the last plane, which the in-place scheme
+// keeps in its own buffer (the slot the pull scheme reads there has another
+// reader, who overwrites it).  Every slot has one reader per step, so each
+// slot is read and then written by one thread, and after every odd step the
+// array is the pull scheme's state again, value for value.
+struct AaSource {
+    unsigned off;  // slot offset (slot true)
+    float val;     // the value otherwise
+    bool slot;
+};
+
+// The source of direction q at cell (x, y, z) on the step `step`, by the pull
+// rules in their order: no-slip, free-slip, periodic wrap, x inlet / outlet.
+__device__ __forceinline__ AaSource aa_source(const DevDomain* D, int q, int x, int y, int z, long long step)
 {
     const int n[3] = {D->nx, D->ny, D->nz};
     const int p[3] = {x, y, z};
     const int c[3] = {qcx(q), qcy(q), qcz(q)};
-    int s[3];
+    const unsigned N = (unsigned)D->N;
+    AaSource r;
+    r.off = 0u;
+    r.val = 0.0f;
+    r.slot = true;
+    int s[3], cm[3];
+    bool wall = false;
     for (int a = 0; a < 3; ++a) {
         s[a] = p[a] - c[a];
-        if (s[a] < 0 || s[a] >= n[a]) {
-            if (D->bc[a] != BC_PERIODIC)
-                return (unsigned)(26 - q) * (unsigned)D->N + (((unsigned)z * (unsigned)n[1] + (unsigned)y) * (unsigned)n[0] + (unsigned)x);
-            s[a] += s[a] < 0 ? n[a] : -n[a];
-        }
+        cm[a] = c[a];
+        if (D->bc[a] == BC_NOSLIP && (s[a] < 0 || s[a] >= n[a])) wall = true;
     }
-    return (unsigned)q * (unsigned)D->N + (((unsigned)s[2] * (unsigned)n[1] + (unsigned)s[1]) * (unsigned)n[0] + (unsigned)s[0]);
+    if (wall) {
+        r.off = (unsigned)(26 - q) * N + (((unsigned)z * (unsigned)n[1] + (unsigned)y) * (unsigned)n[0] + (unsigned)x);
+        return r;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (D->bc[a] == BC_FREESLIP && (s[a] < 0 || s[a] >= n[a])) {
+            cm[a] = -c[a];
+            s[a] = p[a];
+        }
+    for (int a = 0; a < 3; ++a)
+        if (D->bc[a] == BC_PERIODIC) s[a] = s[a] < 0 ? s[a] + n[a] : (s[a] >= n[a] ? s[a] - n[a] : s[a]);
+    if (D->bc[0] == BC_INOUT && (s[0] < 0 || s[0] >= n[0])) {
+        // ghost of the inlet (c_x = +1) or the outlet copy of the last plane (c_x = -1)
+        const float* buf = s[0] < 0 ? D->inflow_ghost[step & 1] : D->outlet[step & 1];
+        r.val = buf[((cm[2] + 1) * 3 + (cm[1] + 1)) * (n[1] * n[2]) + s[2] * n[1] + s[1]];
+        r.slot = false;
+        return r;
+    }
+    const int qm = (cm[2] + 1) * 9 + (cm[1] + 1) * 3 + (cm[0] + 1);
+    r.off = (unsigned)qm * N + (((unsigned)s[2] * (unsigned)n[1] + (unsigned)s[1]) * (unsigned)n[0] + (unsigned)s[0]);
+    return r;
 }
 
-// The even step's loads and stores of a cell next to a no-slip wall, out of
-// line (few cells take them).
-template <typename T>
-__device__ __noinline__ void aa_wall_load(const DevDomain* D, const T* f, int x, int y, int z, float* h)
-{
-    for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldw(f + aa_even_offset(D, q, x, y, z));
-}
-template <typename T>
-__device__ __noinline__ void aa_wall_store(const DevDomain* D, T* f, int x, int y, int z, const float* h)
-{
-    for (int q = 0; q < 27; ++q) Io<T>::st(f + aa_even_offset(D, 26 - q, x, y, z), h[q]);
-}
-
-// Neighbour rows and columns of cell (x, y, z) for the even step away from
-// walls: source coordinates for c = -1, 0, +1 (wrapped on periodic axes), and
-// whether the cell touches a no-slip face.
+// Neighbour rows and columns of cell (x, y, z) away from the wall faces:
+// source coordinates for c = -1, 0, +1 (wrapped on periodic axes, clamped at
+// the x inlet and outlet, whose cells replace those values), and whether the
+// cell lies on a no-slip or free-slip face.
 struct AaNbr {
-    unsigned xs[3], row[3][3];
-    bool wall;
+    unsigned xs[3], ys[3], zs[3];
+    bool face;
 };
 __device__ __forceinline__ AaNbr aa_neighbours(const DevDomain* D, int x, int y, int z)
 {
     const int nx = D->nx, ny = D->ny, nz = D->nz;
     int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
     AaNbr r;
-    r.wall = false;
+    r.face = false;
     if (D->bc[0] == BC_PERIODIC) { if (xm < 0) xm += nx; if (xp >= nx) xp -= nx; }
-    else { r.wall = r.wall || x == 0 || x == nx - 1; }
+    else if (D->bc[0] == BC_INOUT) { xm = max(xm, 0); xp = min(xp, nx - 1); }
+    else { r.face = r.face || x == 0 || x == nx - 1; }
     if (D->bc[1] == BC_PERIODIC) { if (ym < 0) ym += ny; if (yp >= ny) yp -= ny; }
-    else { r.wall = r.wall || y == 0 || y == ny - 1; }
+    else { r.face = r.face || y == 0 || y == ny - 1; }
     if (D->bc[2] == BC_PERIODIC) { if (zm < 0) zm += nz; if (zp >= nz) zp -= nz; }
-    else { r.wall = r.wall || z == 0 || z == nz - 1; }
+    else { r.face = r.face || z == 0 || z == nz - 1; }
     r.xs[0] = (unsigned)xp; r.xs[1] = (unsigned)x; r.xs[2] = (unsigned)xm;
-    const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
-    const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) r.row[k][j] = (zs[k] * (unsigned)ny + ys[j]) * (unsigned)nx;
+    r.ys[0] = (unsigned)yp; r.ys[1] = (unsigned)y; r.ys[2] = (unsigned)ym;
+    r.zs[0] = (unsigned)zp; r.zs[1] = (unsigned)z; r.zs[2] = (unsigned)zm;
     return r;
 }
-
-// The time step on a single PDF array (the AA pattern), lattices with periodic
-// and no-slip faces and no rotor.  The array holds the pull scheme's state
-// A[q][x] = f*_q(x, n-1) before every even step.  A cell reads its 27
-// populations from slots s_q, collides, and writes f*_q to the slot s_qbar it
-// read for the opposite direction:
-//  even step: s_q = the pull source (bounce-back at walls), aa_even_offset;
-//  odd step: s_q = A[qbar][x], so f*_q lands in A[q][x].
-// Each slot is read and then written by one thread only, and after the odd
-// step the array is the pull scheme's state again, value for value.  One
-// launch per step; CTAs cover single-plane tiles.
-template <int COLL, typename T, bool ODD>
-__global__ void __launch_bounds__(256, COLL == COLL_CUMULANT ? 4 : 3) k_step_aa(const StepArgs A)
+__device__ __forceinline__ unsigned aa_row(const AaNbr& nb, int k, int j, int ny, int nx)
 {
+    return (nb.zs[k] * (unsigned)ny + nb.ys[j]) * (unsigned)nx;
+}
+
+// The in-place update of a cell on a no-slip or free-slip face, out of line
+// (few cells take it, and the direct path then needs no stack): every source
+// by the pull rules (aa_source), the inlet ghost for step n+1, the outlet copy.
+// Returns (mass, momentum) of the cell for the diagnostic sums.
+template <int COLL, typename T, bool ODD, bool ROTOR>
+__device__ __noinline__ float4 aa_face_cell(const DevDomain* D, int x, int y, int z, long long step, int n_cull,
+                                            const float4* s_pos, const float4* s_frc, const int* s_tag)
+{
+    T* f = (T*)D->f[0];
+    const unsigned uN = (unsigned)D->N;
+    const int nx = D->nx, ny = D->ny;
+    const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+    float h[27];
+    for (int q = 0; q < 27; ++q) {
+        const AaSource S = aa_source(D, q, x, y, z, step);
+        // odd steps read A[qbar][x] wherever the even rule names a slot
+        h[q] = !S.slot ? S.val : Io<T>::ldw(f + (ODD ? (unsigned)(26 - q) * uN + cell : S.off));
+    }
+    const bool inout = D->bc[0] == BC_INOUT;
+    if (inout && x == 0) write_inlet_ghost(D, step + 1, y, z);
+    float F[3] = {D->body[0], D->body[1], D->body[2]};
+    if (ROTOR) rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
+    float m, jx, jy, jz;
+    if (COLL == COLL_CUMULANT)
+        collide_cumulant(h, F[0], F[1], F[2], D->omega, m, jx, jy, jz);
+    else
+        collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, m, jx, jy, jz);
+    if (inout && x == nx - 1) {
+        float* ob = D->outlet[(step + 1) & 1];
+        const int plane = ny * D->nz, col = z * ny + y;
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) ob[(k * 3 + j) * plane + col] = Io<T>::round(h[k * 9 + j * 3]);
+    }
+    for (int q = 0; q < 27; ++q) {
+        if (ODD) {
+            Io<T>::st(f + ((unsigned)q * uN + cell), h[q]);
+        } else {
+            const AaSource S = aa_source(D, 26 - q, x, y, z, step);  // the slot read for the opposite direction
+            if (S.slot) Io<T>::st(f + S.off, h[q]);                  // else f*_q leaves the lattice
+        }
+    }
+    return make_float4(m, jx, jy, jz);
+}
+
+// The in-place update of one cell (x, y, z), for the bulk and the rotor
+// launches.  ROTOR: the cell lies in a rotor tile and adds the regularised
+// blade force.  Returns the cell's mass and momentum contributions.  Cells on
+// a wall face take aa_face_cell; the x inlet and outlet cells stay on the
+// direct path: the nine directions that cross the face are read from the
+// inlet ghosts or the outlet copy, and the nine post-collision values that
+// leave through it are not stored.
+template <int COLL, typename T, bool ODD, bool ROTOR>
+__device__ __forceinline__ void aa_cell(const DevDomain* D, int x, int y, int z, long long step, int n_cull,
+                                        const float4* s_pos, const float4* s_frc, const int* s_tag, float& m, float& jx,
+                                        float& jy, float& jz)
+{
+    T* f = (T*)D->f[0];
+    const unsigned uN = (unsigned)D->N;
+    const int nx = D->nx, ny = D->ny;
+    const bool inout = D->bc[0] == BC_INOUT;
+    float h[27];
+    {
+        const AaNbr nb = aa_neighbours(D, x, y, z);
+        if (nb.face) {
+            const float4 r = aa_face_cell<COLL, T, ODD, ROTOR>(D, x, y, z, step, n_cull, s_pos, s_frc, s_tag);
+            m = r.x;
+            jx = r.y;
+            jy = r.z;
+            jz = r.w;
+            return;
+        }
+        if (ODD) {
+            const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldw(f + ((unsigned)(26 - q) * uN + cell));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 27; ++q)
+                h[q] = Io<T>::ldw(f + ((unsigned)q * uN + aa_row(nb, q / 9, (q / 3) % 3, ny, nx) + nb.xs[q % 3]));
+        }
+        if (inout && (x == 0 || x == nx - 1)) {
+            // across the inlet: ghosts of the columns (y - c_y, z - c_z); across the
+            // outlet: the last plane's copies there (zero-gradient)
+            // (two branches: a run-time index into h would put h in local memory)
+            const int plane = ny * D->nz;
+            if (x == 0) {
+                const float* gb = D->inflow_ghost[step & 1];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        h[k * 9 + j * 3 + 2] = gb[(k * 3 + j) * plane + (int)nb.zs[k] * ny + (int)nb.ys[j]];
+            } else {
+                const float* ob = D->outlet[step & 1];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        h[k * 9 + j * 3] = ob[(k * 3 + j) * plane + (int)nb.zs[k] * ny + (int)nb.ys[j]];
+            }
+        }
+    }
+    if (inout && x == 0) write_inlet_ghost(D, step + 1, y, z);
+    float F[3] = {D->body[0], D->body[1], D->body[2]};
+    if (ROTOR) rotor_force(D, step, x, y, z, n_cull, s_pos, s_frc, s_tag, F);
+    if (COLL == COLL_CUMULANT)
+        collide_cumulant(h, F[0], F[1], F[2], D->omega, m, jx, jy, jz);
+    else
+        collide_srt_smag(h, F[0], F[1], F[2], D->tau0, D->smag_c2, m, jx, jy, jz);
+    if (inout && x == nx - 1) {
+        // the outlet copy for step n+1: f*_q of the last plane, directions with
+        // c_x = -1, as the array would hold it (rounded to the storage type)
+        float* ob = D->outlet[(step + 1) & 1];
+        const int plane = ny * D->nz, col = z * ny + y;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) ob[(k * 3 + j) * plane + col] = Io<T>::round(h[k * 9 + j * 3]);
+    }
+    // the store slots are the load slots, recomputed from opaque copies of
+    // the inputs: kept live across the collision they would spill
+    unsigned long long fa = (unsigned long long)f;
+    int xo = x, yo = y, zo = z;
+    asm volatile("" : "+l"(fa), "+r"(xo), "+r"(yo), "+r"(zo));
+    f = (T*)fa;
+    if (ODD) {
+        const unsigned cell = ((unsigned)zo * (unsigned)ny + (unsigned)yo) * (unsigned)nx + (unsigned)xo;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Io<T>::st(f + ((unsigned)q * uN + cell), h[q]);
+    } else {
+        const AaNbr nb = aa_neighbours(D, xo, yo, zo);
+        const bool at_in = inout && xo == 0, at_out = inout && xo == nx - 1;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            // f*_q goes to the slot read for the opposite direction, unless it
+            // leaves through the inlet or the outlet
+            if ((qcx(q) == -1 && at_in) || (qcx(q) == 1 && at_out)) continue;
+            const int p = 26 - q;
+            Io<T>::st(f + ((unsigned)p * uN + aa_row(nb, p / 9, (p / 3) % 3, ny, nx) + nb.xs[p % 3]), h[q]);
+        }
+    }
+}
+
+// The time step on a single PDF array (the AA pattern), as two launches like
+// k_step: ROTOR over the rotor tiles (element culling, force gather, and in
+// the last rotor tile of a lattice the actuator line of the next step, whose
+// sampling reads the array in the layout this step leaves), then the rest,
+// which may overlap it.  Rotor tiles cover up to kRotorPlanes planes, one
+// after the other; bulk tiles one plane.
+template <int COLL, typename T, bool ODD, bool ROTOR>
+__global__ void __launch_bounds__(256, ROTOR ? 2 : (COLL == COLL_CUMULANT ? 4 : 3)) k_step_aa(const StepArgs A)
+{
+    if (ROTOR) asm volatile("griddepcontrol.launch_dependents;");
+    constexpr int kCull = 128;
     __shared__ double s_red[8][4];
+    __shared__ int s_flag;
+    __shared__ float4 s_pos[ROTOR ? kCull : 1], s_frc[ROTOR ? kCull : 1];
+    __shared__ int s_tag[ROTOR ? kCull : 1];
+    __shared__ int s_cnt[8];
     const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
-    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int z0 = (int)((tile >> 32) & 0xFFFF);
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
     const DevDomain* D = A.dom + tile_lattice(tile);
     const long long step = __ldcg(A.step_slot + A.parity);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (A.write_step && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         A.step_slot[A.parity ^ 1] = step + 1;
         A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
     }
     const bool diag = __ldcg(A.diag_flag + A.parity) != 0;
-    float o_m = 0.0f, o_jx = 0.0f, o_jy = 0.0f, o_jz = 0.0f;
-    if (x < D->nx && y < D->ny) {
-        T* f = (T*)D->f[0];
-        const unsigned uN = (unsigned)D->N;
-        float h[27];
-        bool wall = false;
-        if (ODD) {
-            const unsigned cell = ((unsigned)z * (unsigned)D->ny + (unsigned)y) * (unsigned)D->nx + (unsigned)x;
-#pragma unroll
-            for (int q = 0; q < 27; ++q) h[q] = Io<T>::ldw(f + ((unsigned)(26 - q) * uN + cell));
-        } else {
-            const AaNbr nb = aa_neighbours(D, x, y, z);
-            wall = nb.wall;
-            if (!wall) {
-#pragma unroll
-                for (int q = 0; q < 27; ++q)
-                    h[q] = Io<T>::ldw(f + ((unsigned)q * uN + nb.row[q / 9][(q / 3) % 3] + nb.xs[q % 3]));
-            } else {
-                float hl[27];
-                aa_wall_load<T>(D, f, x, y, z, hl);
-#pragma unroll
-                for (int q = 0; q < 27; ++q) h[q] = hl[q];
+    using Acc = typename std::conditional<ROTOR, double, float>::type;
+    Acc o_m = 0, o_jx = 0, o_jy = 0, o_jz = 0;
+    if constexpr (ROTOR) {
+        const int planes = tile_planes(tile);
+        const int z1 = min(z0 + planes, D->nz);
+        const int n_cull = cull_rotor_elements<kCull>(D, tile, step, z0, z1, s_pos, s_frc, s_tag, s_cnt);
+        if (x < D->nx && y < D->ny) {
+#pragma unroll 1
+            for (int z = z0; z < z1; ++z) {
+                float m, jx, jy, jz;
+                aa_cell<COLL, T, ODD, true>(D, x, y, z, step, n_cull, s_pos, s_frc, s_tag, m, jx, jy, jz);
+                if (diag) {
+                    o_m += m;
+                    o_jx += jx;
+                    o_jy += jy;
+                    o_jz += jz;
+                }
             }
         }
-        float m, jx, jy, jz;
-        if (COLL == COLL_CUMULANT)
-            collide_cumulant(h, D->body[0], D->body[1], D->body[2], D->omega, m, jx, jy, jz);
-        else
-            collide_srt_smag(h, D->body[0], D->body[1], D->body[2], D->tau0, D->smag_c2, m, jx, jy, jz);
-        if (diag) {
-            o_m = m;
-            o_jx = jx;
-            o_jy = jy;
-            o_jz = jz;
+        // last rotor tile of this lattice: actuator line of the next step, from
+        // the array in the layout this step leaves (after an even step the
+        // pulled populations of cell x are its own opposite slots)
+        __syncthreads();
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(D->rotor_counter, 1u);
+            s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
         }
-        // the store slots are the load slots, recomputed from opaque copies of
-        // the inputs: kept live across the collision they would spill
-        unsigned long long fa = (unsigned long long)f;
-        int xo = x, yo = y, zo = z;
-        asm volatile("" : "+l"(fa), "+r"(xo), "+r"(yo), "+r"(zo));
-        f = (T*)fa;
-        if (ODD) {
-            const unsigned cell = ((unsigned)zo * (unsigned)D->ny + (unsigned)yo) * (unsigned)D->nx + (unsigned)xo;
-#pragma unroll
-            for (int q = 0; q < 27; ++q) Io<T>::st(f + ((unsigned)q * uN + cell), h[q]);
-        } else if (!wall) {
-            const AaNbr nb = aa_neighbours(D, xo, yo, zo);
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const int p = 26 - q;  // the slot read for the opposite direction
-                Io<T>::st(f + ((unsigned)p * uN + nb.row[p / 9][(p / 3) % 3] + nb.xs[p % 3]), h[q]);
+        __syncthreads();
+        if (s_flag) {
+            __threadfence();
+            alm_compute<T>(D, (const T*)D->f[0], step + 1, ODD ? 0 : 1);
+            if (tid == 0) *D->rotor_counter = 0u;
+        }
+    } else {
+        if (x < D->nx && y < D->ny) {
+            float m, jx, jy, jz;
+            aa_cell<COLL, T, ODD, false>(D, x, y, z0, step, -1, nullptr, nullptr, nullptr, m, jx, jy, jz);
+            if (diag) {
+                o_m = m;
+                o_jx = jx;
+                o_jy = jy;
+                o_jz = jz;
             }
-        } else {
-            float hl[27];
-#pragma unroll
-            for (int q = 0; q < 27; ++q) hl[q] = h[q];
-            aa_wall_store<T>(D, f, xo, yo, zo, hl);
         }
     }
-    if (diag) diag_close(A, D, step, o_m, o_jx, o_jy, o_jz, s_red);
+    if (diag) diag_close(A, D, step, (double)o_m, (double)o_jx, (double)o_jy, (double)o_jz, s_red);
+    if constexpr (!ROTOR) {
+        if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
+    }
+}
+
+// Outlet copies of the last plane for step `step` from the array's current
+// (pull-scheme) state, after a state change of an in-place lattice.
+template <typename T>
+__global__ void k_outlet_fill(const DevDomain* D, long long step)
+{
+    const int plane = D->ny * D->nz;
+    const T* f = (const T*)D->f[0];
+    float* ob = D->outlet[step & 1];
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < plane; col += gridDim.x * blockDim.x) {
+        const int y = col % D->ny, z = col / D->ny;
+        const long long cell = ((long long)z * D->ny + y) * D->nx + (D->nx - 1);
+        for (int g = 0; g < 9; ++g) ob[g * plane + col] = Io<T>::ldcg(f + (size_t)(g * 3) * D->N + cell);
+    }
 }
 
 // ------------------------------------------------------------------ staged step (TMA bulk copies)
@@ -2007,13 +2219,18 @@ static cudaError_t launch_dependent(void (*kernel)(StepArgs), dim3 grid, dim3 bl
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd)
+cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd,
+                           bool rotor, bool dependent)
 {
-#define LBM_AA_CASE(C, S, T)                                                \
-    if (coll == C && store == S) {                                          \
-        if (odd) k_step_aa<C, T, true><<<grid, block, 0, s>>>(a);           \
-        else k_step_aa<C, T, false><<<grid, block, 0, s>>>(a);              \
-        return cudaGetLastError();                                          \
+#define LBM_AA_ONE(C, T, O)                                                                        \
+    if (rotor) k_step_aa<C, T, O, true><<<grid, block, 0, s>>>(a);                                 \
+    else if (dependent) return launch_dependent(k_step_aa<C, T, O, false>, grid, block, s, a);     \
+    else k_step_aa<C, T, O, false><<<grid, block, 0, s>>>(a);
+#define LBM_AA_CASE(C, S, T)                         \
+    if (coll == C && store == S) {                   \
+        if (odd) { LBM_AA_ONE(C, T, true) }          \
+        else { LBM_AA_ONE(C, T, false) }             \
+        return cudaGetLastError();                   \
     }
     LBM_AA_CASE(COLL_CUMULANT, STORE_FP32, float)
     LBM_AA_CASE(COLL_CUMULANT, STORE_BF16, __nv_bfloat16)
@@ -2022,7 +2239,17 @@ cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStrea
     LBM_AA_CASE(COLL_SRT_SMAG, STORE_BF16, __nv_bfloat16)
     LBM_AA_CASE(COLL_SRT_SMAG, STORE_FP16, __half)
 #undef LBM_AA_CASE
+#undef LBM_AA_ONE
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_outlet_fill(int store, const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s)
+{
+    const int g = grid_for((long long)h.ny * h.nz, 256);
+    if (store == STORE_FP32) k_outlet_fill<float><<<g, 256, 0, s>>>(d_dom_inst, step);
+    else if (store == STORE_BF16) k_outlet_fill<__nv_bfloat16><<<g, 256, 0, s>>>(d_dom_inst, step);
+    else k_outlet_fill<__half><<<g, 256, 0, s>>>(d_dom_inst, step);
+    return cudaGetLastError();
 }
 
 static cudaError_t launch_dependent_bulk(void (*kernel)(StepArgs, BulkParams), dim3 grid, dim3 block, cudaStream_t s,
@@ -2042,7 +2269,7 @@ static cudaError_t launch_dependent_bulk(void (*kernel)(StepArgs, BulkParams), d
 }
 
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
-                        bool dependent, const BulkParams* bulk)
+                        bool dependent, const BulkParams* bulk, bool diag_step)
 {
     const bool march = a.tile_z > 1;
 #define LBM_STEP_CASE(C, S, T)                                                                        \
@@ -2060,8 +2287,11 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
             if (dependent) return launch_dependent(k_step<C, T, false, false>, grid, block, s, a);    \
             k_step<C, T, false, false><<<grid, block, 0, s>>>(a);                                     \
         } else {                                                                                      \
-            if (dependent) return launch_dependent_bulk(k_bulk<C, T>, grid, block, s, a, *bulk);      \
-            k_bulk<C, T><<<grid, block, 0, s>>>(a, *bulk);                                            \
+            void (*kb)(StepArgs, BulkParams) =                                                        \
+                diag_step ? (a.n_inst == 1 ? k_bulk<C, T, true, true> : k_bulk<C, T, true, false>)    \
+                          : (a.n_inst == 1 ? k_bulk<C, T, false, true> : k_bulk<C, T, false, false>); \
+            if (dependent) return launch_dependent_bulk(kb, grid, block, s, a, *bulk);                \
+            kb<<<grid, block, 0, s>>>(a, *bulk);                                                      \
         }                                                                                             \
         return cudaGetLastError();                                                                    \
     }

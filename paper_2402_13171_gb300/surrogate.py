@@ -289,5 +289,31 @@ def settle_step(wm, ref, tol):
     return None
 
 
+def running_mean_changes(wm):
+    """Relative L2 change of the running mean of hub-plane u_x over each window:
+    with R_k the mean of the first k window means, ||R_k - R_(k-1)|| / ||R_k||
+    for k >= 2 (at the window ends 2, 3, ... windows in)."""
+    out = []
+    acc = np.zeros_like(wm.means[0]) if wm.means else None
+    prev = None
+    for k, (m, e) in enumerate(zip(wm.means, wm.ends), start=1):
+        acc = acc + m
+        r = acc / k
+        if prev is not None:
+            out.append((e, float(np.linalg.norm(r - prev) / np.linalg.norm(r))))
+        prev = r
+    return out
+
+
+def running_mean_settle_step(wm, tol=1e-3):
+    """First window end at which the running mean of hub-plane u_x changes by
+    less than tol (relative L2) over one window: the converged-mean criterion
+    of the farm workload.  None if it never does."""
+    for e, c in running_mean_changes(wm):
+        if c < tol:
+            return e
+    return None
+
+
 def window_errors(wm, ref):
     return [float(np.linalg.norm(m - ref) / np.linalg.norm(ref)) for m in wm.means]

@@ -3,8 +3,10 @@
 After every even number of steps the single AA array holds exactly the pull
 scheme's state, so the two are compared bitwise, on periodic and no-slip
 lattices, both collisions and 16-bit storage, through graph replays and single
-launches; odd step counts refuse state access; the PDF memory is halved; and
-the oracle confirms the pull scheme these are compared with (one step)."""
+launches; with the rotor workload's inlet noise, outlet and actuator line; with
+free-slip walls; on a two-rotor log-law lattice; odd step counts refuse state
+access; the PDF memory is halved; and the oracle confirms the pull scheme these
+are compared with."""
 import numpy as np
 import pytest
 
@@ -92,9 +94,6 @@ def test_inplace_halves_pdf_memory_and_refuses_what_it_does_not_take():
     ga = lbm.Lattice.create(nx, ny, nz, inplace=True)
     m2 = torch.cuda.memory_allocated()
     assert (m1 - m0) - (m2 - m1) >= fbytes            # one PDF array fewer
-    dom, turb = I.single_turbine_case(64, 32, 32, diameter=8.0, elements_per_blade=4)
-    with pytest.raises(lbm.LbmError, match="unsupported"):
-        ga.add_turbine(**turb)
     with pytest.raises(lbm.LbmError, match="unsupported"):
         ga.set_tile(32, 4, 2)
     ga.step(3)
@@ -127,3 +126,109 @@ def test_inplace_batch_equals_separate_two_array_runs():
         g.step(6)
         np.testing.assert_array_equal(L.pdfs(), g.pdfs())
         g.destroy()
+
+
+def _rotor_pair(dom, turbs, storage="fp32", diag_every=0):
+    kw = dict(collision=dom.get("collision", "cumulant"), nu=dom["nu"], smag_c=dom.get("smag_c", 0.1), storage=storage,
+              bc=dom["bc"], seed=dom["seed"], diag_every=diag_every)
+    out = []
+    for inplace in (False, True):
+        g = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], inplace=inplace, **kw)
+        g.set_inflow(u_ref=dom["u_ref"], kind=dom.get("inflow_kind", 0), z0=dom.get("z0", 0.1),
+                     z_ref=dom.get("z_ref", 1.0), noise_rel=dom["noise_rel"])
+        for t in turbs:
+            g.add_turbine(**t)
+        out.append(g)
+    return out
+
+
+def _same_run(g2, ga, n_turb, counts=(10, 1, 1, 2, 8, 6)):
+    for n in counts:   # graph replays of 8 and 2, single odd and even launches
+        g2.step(n)
+        ga.step(n)
+        if ga.step_count() % 2:
+            continue
+        np.testing.assert_array_equal(ga.pdfs(), g2.pdfs())
+        for t in range(n_turb):
+            th2, tq2, ef2, ep2 = g2.loads(t, elements=True)
+            tha, tqa, efa, epa = ga.loads(t, elements=True)
+            assert (tha, tqa) == (th2, tq2)
+            np.testing.assert_array_equal(efa, ef2)
+            np.testing.assert_array_equal(epa, ep2)
+
+
+@pytest.mark.parametrize("collision,storage,kernel", [("cumulant", "fp32", "gauss"), ("cumulant", "bf16", "gauss"),
+                                                      ("srt_smag", "fp32", "roma")])
+def test_inplace_rotor_inlet_outlet_equals_two_arrays_bitwise(collision, storage, kernel):
+    """The rotor workload's scaled-down case on one array: velocity inlet with
+    noise, zero-gradient outlet, the actuator line (its sampling reads the array
+    in the layout each step leaves) -- bit for bit the two-array run at every
+    even step, loads and element forces included, with diagnostics."""
+    dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777, kernel=kernel)
+    dom["collision"] = collision
+    g2, ga = _rotor_pair(dom, [turb], storage, diag_every=4)
+    assert ga.launches_per_step() == 2
+    _same_run(g2, ga, 1)
+    d2, s2 = g2.diagnostics()
+    da, sa = ga.diagnostics()
+    assert s2 == sa
+    np.testing.assert_allclose(da, d2, rtol=0, atol=1e-9)
+    g2.destroy()
+    ga.destroy()
+
+
+@pytest.mark.parametrize("bc", [("inout", "periodic", "freeslip"), ("freeslip", "noslip", "freeslip"),
+                                ("inout", "freeslip", "noslip"), ("periodic", "freeslip", "periodic")])
+def test_inplace_free_slip_and_inlet_faces_equal_two_arrays_bitwise(bc):
+    """Free-slip faces and their corners with inlet, outlet and no-slip faces
+    on one array: a slot a free-slip face reflects into has one reader, so the
+    write-back into the slot read stays exact."""
+    nx, ny, nz = 23, 9, 11
+    kw = dict(nu=0.02, bc=bc, body_force=(2e-6, 0, -1e-6), seed=77)
+    rho, u, fneq = I.random_state(nx, ny, nz, seed=5, u_mean=(0.04, 0.01, 0.0))
+    out = []
+    for inplace in (False, True):
+        g = lbm.Lattice.create(nx, ny, nz, inplace=inplace, **kw)
+        if bc[0] == "inout":
+            g.set_inflow(u_ref=(0.04, 0.01, 0.0), noise_rel=0.01)
+        g.init_fields(rho, u, fneq)
+        out.append(g)
+    g2, ga = out
+    _same_run(g2, ga, 0)
+    g2.destroy()
+    ga.destroy()
+
+
+def test_inplace_log_law_farm_equals_two_arrays_bitwise():
+    """The scaled-down farm on one array: log-law inflow with noise, free-slip
+    bottom and top, periodic y, two yawed rotors."""
+    dom, turbs = I.small_farm_case()
+    g2, ga = _rotor_pair(dom, turbs, diag_every=5)
+    _same_run(g2, ga, 2, counts=(8, 2, 1, 1, 10))
+    g2.destroy()
+    ga.destroy()
+
+
+def test_inplace_rotor_step_pair_matches_oracle_and_resumes_bitwise():
+    """One step pair of the in-place rotor case against the FP64 oracle at the
+    parity bound, and a checkpoint of the in-place lattice resumes bit for bit."""
+    from cases import oracle_sim
+    dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777)
+    _, ga = _rotor_pair(dom, [turb])
+    s = oracle_sim(dom, [turb])
+    s.init_fields()
+    ga.step(2)
+    s.step(2)
+    assert max_du(ga, s) <= 1e-6
+    th, tq = ga.loads(0)
+    assert th == pytest.approx(s.loads[0, 0], rel=5e-5)
+    blob = ga.state()
+    ga.step(6)
+    gb = _rotor_pair(dom, [turb])[1]
+    gb.step(4)
+    gb.set_state(blob)
+    gb.step(6)
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    assert ga.loads(0) == gb.loads(0)
+    ga.destroy()
+    gb.destroy()

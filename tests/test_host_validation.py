@@ -109,14 +109,12 @@ def test_static_alm_rejects_bad_rotors_on_the_host(over):
 
 
 @pytest.mark.parametrize("kw,code", [
-    (dict(inplace=True, bc=("inout", "periodic", "periodic")), UNSUPPORTED),
-    (dict(inplace=True, bc=("periodic", "freeslip", "periodic")), UNSUPPORTED),
     (dict(inplace=True, tile=(32, 4, 2)), UNSUPPORTED),
     (dict(inplace=True, tile=(64, 1, 1, 1)), UNSUPPORTED),
 ])
 def test_inplace_scheme_limits_are_checked_on_the_host(kw, code):
-    """The in-place (AA) scheme takes periodic and no-slip faces and
-    single-plane direct tiles only; anything else is refused at creation."""
+    """The in-place (AA) scheme takes single-plane direct tiles only;
+    marching or staged tiles are refused at creation."""
     assert _create(**kw) == code
 
 
