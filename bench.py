@@ -800,10 +800,10 @@ TILE_CANDIDATES = [(32, 4, 1, 0), (32, 2, 1, 0), (32, 8, 1, 0), (64, 2, 1, 0), (
 
 def run_tilesweep(args):
     """The single-rotor workload at every tile candidate of the tuner: the
-    k_step device time per step (CUDA events over --steps steps after
-    --warmup) and its fraction of the HBM roofline.  Under `ncu --metrics
-    dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_step` it gives the
-    DRAM bytes of every tile in one pass."""
+    device time per step (CUDA events over --steps steps after --warmup) and
+    its fraction of the HBM roofline.  CUDA events only: DRAM bytes are taken
+    by a separate capture of one step at one tile (`bench.py --tile ...` under
+    ncu with -c 2)."""
     import torch
 
     from paper_2402_13171_gb300 import build as B

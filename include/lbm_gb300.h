@@ -11,11 +11,12 @@
  *   5. pull streaming with boundary rules, and
  *   6. cumulant collision (Geier et al. 2015, Sec. 2.1) or BGK-Smagorinsky with Guo forcing
  *      (Sec. 2.1, lattice Boltzmann equation with source term).
- * Steps 5-6 run fused in one kernel over the lattice, launched twice per time
- * step: over the tiles around the rotors, then over the rest, the second
- * overlapping the first.  Steps 1-4 of step n+1 run inside the rotor launch of
- * step n as soon as the cells around the rotor are written, under the bulk
- * launch, so the actuator line adds no serial gap.
+ * Steps 5-6 run fused in one pass over the lattice, launched per time step
+ * over the tiles around the rotors, then (where there are any) over the tiles
+ * on a no-slip or free-slip face, then over the rest, each launch overlapping
+ * the one before.  Steps 1-4 of step n+1 run inside the rotor launch of step n
+ * as soon as the cells around the rotor are written, under the bulk launch,
+ * so the actuator line adds no serial gap.
  *
  * Conventions shared by every call:
  *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, relaxation rate omega = 1/(3 nu + 1/2).
@@ -301,10 +302,12 @@ lbm_status lbm_get_kernel_time(lbm_ctx* ctx, double* mean_ms, long long* steps);
  * the storage type) and the number of cells of one step (all lattices). */
 lbm_status lbm_get_traffic_model(lbm_ctx* ctx, double* bytes_per_cell, long long* cells_per_step);
 
-/* Kernel launches of one time step with the current tile and rotors: 2 (the
- * tiles around the rotors, then the rest) or 1 (staged rows, or a lattice
- * without rotor tiles).  Uploads pending descriptors first (stream-ordered).
- * Errors: INVALID_ARG for a null output. */
+/* Kernel launches of one time step with the current tile and rotors: the
+ * tiles around the rotors, then the tiles with a cell on a no-slip or
+ * free-slip face, then the rest (each launch only where it has tiles; the
+ * in-place scheme takes the last two together; staged rows are one launch).
+ * Uploads pending descriptors first (stream-ordered).  Errors: INVALID_ARG
+ * for a null output. */
 lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches);
 
 /* Actuator-line evaluation for callers that cannot allocate device memory:

@@ -66,6 +66,7 @@ struct Batch {
     long long prof_n = 0;
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [long?][start parity]
     unsigned n_rotor = 0;                 // rotor tiles at the head of the work list
+    unsigned n_face = 0;                  // then the tiles with a no-slip or free-slip face cell
     int rotor_planes = 1;                 // planes of the deepest rotor tile
     int inplace = 0;                      // one PDF array, AA pattern
     long long* d_probe = nullptr;   // probe cell list and results, grown on demand
@@ -296,7 +297,7 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
 lbm_status sync_descriptors(Batch* b)
 {
     if (!b->dirty) return LBM_OK;
-    std::vector<unsigned long long> rotor, rest;
+    std::vector<unsigned long long> rotor, face, rest;
     // rotor tiles: the z-blocks of a column that reach a rotor box, runs of them
     // merged up to kRotorPlanes planes (not for the staged kernel's row segments)
     const int merge = b->staged ? 1 : std::max(1, kRotorPlanes / b->tile_z);
@@ -341,7 +342,15 @@ lbm_status sync_descriptors(Batch* b)
                     const int p = planes[((size_t)k * nyb + j) * nxb + l];
                     const int z = k * b->tile_z, y0 = j * b->tile_y, x0 = l * b->tile_x;
                     if (p == 0) {
-                        rest.push_back(pack_tile((int)i, z, y0, x0, false));
+                        // a cell of the tile on a no-slip or free-slip face: the general kernel
+                        const int lo[3] = {x0, y0, z}, ext[3] = {b->tile_x, b->tile_y, b->tile_z};
+                        const int n3[3] = {I.h.nx, I.h.ny, I.h.nz};
+                        bool on_face = false;
+                        for (int a3 = 0; a3 < 3; ++a3)
+                            if ((I.h.bc[a3] == BC_NOSLIP || I.h.bc[a3] == BC_FREESLIP) &&
+                                (lo[a3] == 0 || lo[a3] + ext[a3] - 1 >= n3[a3] - 1))
+                                on_face = true;
+                        (on_face ? face : rest).push_back(pack_tile((int)i, z, y0, x0, false));
                     } else if (p > 0) {
                         rotor.push_back(pack_tile((int)i, z, y0, x0, true, p));
                         rotor_planes = std::max(rotor_planes, p);
@@ -355,6 +364,7 @@ lbm_status sync_descriptors(Batch* b)
             CK(cudaMemcpyAsync(I.d_turb, dt.data(), sizeof(DevTurbine) * dt.size(), cudaMemcpyHostToDevice, b->stream));
     }
     std::vector<unsigned long long> tiles = rotor;
+    tiles.insert(tiles.end(), face.begin(), face.end());
     tiles.insert(tiles.end(), rest.begin(), rest.end());
     if (tiles.size() > b->tiles_cap) {
         if (b->d_tiles) dfree(b, b->d_tiles);
@@ -365,6 +375,7 @@ lbm_status sync_descriptors(Batch* b)
     }
     b->n_tiles = (unsigned)tiles.size();
     b->n_rotor = (unsigned)rotor.size();
+    b->n_face = (unsigned)face.size();
     b->rotor_planes = rotor_planes;
     CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(unsigned long long) * tiles.size(), cudaMemcpyHostToDevice,
                        b->stream));
@@ -394,10 +405,7 @@ StepArgs step_args(Batch* b, int parity)
     a.tile_z = b->tile_z;
     a.staged = b->staged;
     a.wait_cycles = b->wait_cycles;
-    a.walls = 0;
-    for (auto& I : b->inst)
-        for (int ax = 0; ax < 3; ++ax)
-            if (I.h.bc[ax] == BC_NOSLIP || I.h.bc[ax] == BC_FREESLIP) a.walls = 1;
+    a.trigger = 0;
     return a;
 }
 
@@ -428,20 +436,35 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
                        false));
         return LBM_OK;
     }
-    const unsigned R = b->n_rotor, Nb = b->n_tiles - b->n_rotor;
-    StepArgs ar = a, ab = a;
-    ar.n_tiles = R;
-    ar.write_step = Nb == 0 ? 1 : 0;
-    ar.tile_z = b->rotor_planes;  // > 1: the marching rotor kernel, each tile over its own planes
-    ab.tiles = b->d_tiles + R;
-    ab.n_tiles = Nb;
+    const unsigned R = b->n_rotor, Nf = b->n_face, Np = b->n_tiles - b->n_rotor - b->n_face;
     if (b->inplace) {
+        // the in-place kernels take every rule themselves: rotor tiles, then the rest
+        const unsigned Nb = Nf + Np;
+        StepArgs ar = a, ab = a;
+        ar.n_tiles = R;
+        ar.write_step = Nb == 0 ? 1 : 0;
+        ab.tiles = b->d_tiles + R;
+        ab.n_tiles = Nb;
         if (R > 0) CK(launch_step_aa(b->coll, b->store, dim3(R), block, b->stream, ar, parity == 1, true, false));
         if (Nb > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nb), block, b->stream, ab, parity == 1, false, R > 0));
         return LBM_OK;
     }
+    // rotor tiles, then the face tiles (the general kernel), then the plain bulk
+    // (k_bulk); each launch may start while the one before still runs, the last
+    // one advances the step counter
+    StepArgs ar = a, af = a, ap = a;
+    ar.n_tiles = R;
+    ar.write_step = (Nf + Np) == 0 ? 1 : 0;
+    ar.tile_z = b->rotor_planes;  // > 1: the marching rotor kernel, each tile over its own planes
+    af.tiles = b->d_tiles + R;
+    af.n_tiles = Nf;
+    af.write_step = Np == 0 ? 1 : 0;
+    af.trigger = Np > 0 ? 1 : 0;
+    ap.tiles = b->d_tiles + R + Nf;
+    ap.n_tiles = Np;
     if (R > 0) CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));
-    if (Nb > 0) {
+    if (Nf > 0) CK(launch_step(b->coll, b->store, dim3(Nf), block, b->stream, af, false, R > 0));
+    if (Np > 0) {
         BulkParams bp{};
         for (size_t i = 0; i < b->inst.size(); ++i) {
             const DevDomain& h = b->inst[i].h;
@@ -458,7 +481,9 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
             L.f[0] = h.f[0];
             L.f[1] = h.f[1];
         }
-        CK(launch_step(b->coll, b->store, dim3(Nb), block, b->stream, ab, false, R > 0, &bp, diag_step));
+        const bool tiled = b->tile_z == 1;  // k_bulk takes single-plane tiles
+        CK(launch_step(b->coll, b->store, dim3(Np), block, b->stream, ap, false, R + Nf > 0, tiled ? &bp : nullptr,
+                       diag_step));
     }
     return LBM_OK;
 }
@@ -1477,7 +1502,11 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
     // the same split as launch_one
-    *launches = b->staged ? 1 : (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
+    if (b->staged) *launches = 1;
+    else if (b->inplace) *launches = (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
+    else
+        *launches = (b->n_rotor > 0 ? 1 : 0) + (b->n_face > 0 ? 1 : 0) +
+                    (b->n_tiles > b->n_rotor + b->n_face ? 1 : 0);
     return LBM_OK;
 }
 

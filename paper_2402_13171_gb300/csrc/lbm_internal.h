@@ -106,7 +106,7 @@ struct StepArgs {
     int tile_z;                         // planes per CTA (1: no marching); for the rotor launch the deepest rotor tile
     int staged;                         // rows staged in shared memory by persistent CTAs
     long long wait_cycles;              // bound of the staged step's copy-barrier waits (SM clock cycles)
-    int walls;                          // some lattice has a no-slip or free-slip face
+    int trigger;                        // a non-rotor launch followed by a dependent launch: let it start early
 };
 
 // Per-lattice values the bulk launch reads for every cell, passed in its
@@ -168,8 +168,8 @@ inline bool turbine_values_finite(const alm_turbine_desc* d)
 // actuator line of the next step) rather than over the rest.  dependent: a
 // bulk launch that directly follows its own step's rotor launch on the stream
 // and may overlap it (programmatic stream serialization).
-// bulk: the lattices' per-cell parameters for the bulk kernel of lattices
-// without wall faces (nullptr: the general kernel); diag_step: the step is a
+// bulk: the lattices' per-cell parameters for the bulk kernel over the tiles
+// without a wall-face cell (nullptr: the general kernel); diag_step: the step is a
 // diagnostic step (the bulk kernel then carries the FP64 sums; the general
 // kernels read the step's diagnostic flag on the device).
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,

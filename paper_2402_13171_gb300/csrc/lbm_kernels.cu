@@ -1235,7 +1235,7 @@ __device__ __forceinline__ void diag_close(const StepArgs& A, const DevDomain* D
 template <int COLL, typename T, bool MARCH, bool ROTOR, bool WALLS = true>
 __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMULANT) ? 3 : 4)) k_step(const StepArgs A)
 {
-    if (ROTOR) asm volatile("griddepcontrol.launch_dependents;");
+    if (ROTOR || A.trigger) asm volatile("griddepcontrol.launch_dependents;");
     constexpr int kCull = 128;  // blade elements kept per rotor tile
     __shared__ double s_red[8][4];
     __shared__ int s_flag;
@@ -1310,9 +1310,10 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
     }
 }
 
-// The bulk launch for lattices without no-slip or free-slip faces (y and z
-// then periodic, x periodic or inlet/outlet), which is almost every cell of
-// the workloads: the same update as k_step's bulk path, with the lattice's
+// The bulk launch over the tiles with no cell on a no-slip or free-slip face
+// (their other neighbours wrap on periodic axes or stay inside the lattice,
+// and x may be an inlet/outlet), almost every cell of the workloads: the same
+// update as k_step's bulk path, with the lattice's
 // sizes, rates and array pointers read from the kernel parameters instead of
 // its descriptor in global memory, and no wall code compiled in.  Inlet cells
 // take their nine ghost populations from the inlet buffer.  DIAG: the host
@@ -2283,7 +2284,7 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
             else k_step<C, T, true, false><<<grid, block, 0, s>>>(a);                                 \
         } else if (rotor) {                                                                           \
             k_step<C, T, false, true><<<grid, block, 0, s>>>(a);                                      \
-        } else if (a.walls || !bulk) {                                                                \
+        } else if (!bulk) {                                                                           \
             if (dependent) return launch_dependent(k_step<C, T, false, false>, grid, block, s, a);    \
             k_step<C, T, false, false><<<grid, block, 0, s>>>(a);                                     \
         } else {                                                                                      \

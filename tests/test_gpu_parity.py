@@ -385,8 +385,8 @@ def test_loads_sink_matches_synchronous_reads():
 def test_checkpoint_resume_is_bitwise(storage):
     """A lattice with a rotor, inlet noise and diagnostics, checkpointed after
     11 steps (lbm_get_state) and restored into a lattice with another history:
-    at step 17 PDFs, rotor loads, element forces and diagnostics are bit for
-    bit those of the uninterrupted run."""
+    at step 17 PDFs, rotor loads and element forces are bit for bit those of
+    the uninterrupted run, and the diagnostic sums equal to FP64 rounding."""
     dom, turb = small_rotor_case()
     ga, _ = setup_pair(dom, [turb], inflow=True, storage=storage, diag_every=4)
     ga.step(11)
@@ -404,7 +404,8 @@ def test_checkpoint_resume_is_bitwise(storage):
     np.testing.assert_array_equal(efa, efb)
     np.testing.assert_array_equal(epa, epb)
     assert ga.diagnostics()[1] == gb.diagnostics()[1] == 16
-    np.testing.assert_array_equal(ga.diagnostics()[0], gb.diagnostics()[0])
+    # the FP64 sums add per-CTA partials in arrival order: equal to rounding
+    np.testing.assert_allclose(ga.diagnostics()[0], gb.diagnostics()[0], rtol=1e-12, atol=1e-12)
     # a state of another lattice shape or rotor set is refused
     gc = gpu_lattice(dict(dom, nx=dom["nx"] + 8))
     from paper_2402_13171_gb300 import lbm
