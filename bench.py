@@ -41,8 +41,8 @@ def parse_args():
     p.add_argument("--storage", choices=["fp32", "bf16", "fp16"], default="fp32")
     p.add_argument("--collision", choices=["cumulant", "srt_smag"], default="cumulant")
     p.add_argument("--tile", type=str, default="auto",
-                   help="CTA tile XxY, XxYxZ or XxYxZxS (S = 1: rows staged in shared memory), or 'auto' "
-                        "(the library's autotuner, cached)")
+                   help="CTA tile XxY, XxYxZ or XxYxZxS (S = 1: rows staged in shared memory; S = 2: one cell "
+                        "per thread where the bulk kernel would take two), or 'auto' (the library's autotuner, cached)")
     p.add_argument("--workload", choices=["single", "batch16", "periodic", "precision", "warmstart", "tilesweep"],
                    default="single",
                    help="single: the 256x128x128 rotor case; batch16: 16 seeded rotor lattices stepped by "
@@ -66,6 +66,13 @@ def parse_args():
     if args.kernel != "gauss" and args.workload != "single":
         p.error("--kernel applies to --workload single")
     return args
+
+
+def tile_label(tile):
+    """'XxYxZ' of a (tile_x, tile_y, tile_z, form) tuple, with ' staged' for rows
+    staged in shared memory and ' single' for one cell per thread where the
+    bulk kernel would pair cells."""
+    return "x".join(str(v) for v in tile[:3]) + {0: "", 1: " staged", 2: " single"}.get(int(tile[3]), "")
 
 
 def dist_info():
@@ -401,7 +408,7 @@ def run_ours(args):
         cache = os.path.join(ROOT, "paper_2402_13171_gb300", "_build", "tune_cache.txt")
         lat.autotune(steps=20, cache=cache)
     tx_, ty_, tz_, st_ = lat.tile()
-    tile_used = f"{tx_}x{ty_}x{tz_}" + (" staged" if st_ else "")
+    tile_used = tile_label(lat.tile())
     bytes_per_cell, cells = lat.traffic_model()
     lat.step(args.warmup)
     lat.sync()
@@ -626,7 +633,7 @@ def run_precision(args):
         mlups = cells * timed_steps / (timed_ms * 1e-3) / 1e6
         out[storage] = {"mean_ux": mean[:, 0], "mlups": mlups,
                         "hbm_frac": bpc * cells * timed_steps / (timed_ms * 1e-3) / 1e9 / load_peaks()[0],
-                        "tile": "x".join(map(str, lat.tile()[:3])) + (" staged" if lat.tile()[3] else "")}
+                        "tile": tile_label(lat.tile())}
         lat.destroy()
     errors = {}
     for storage in ("fp32_twin", "bf16", "fp16"):
@@ -827,7 +834,7 @@ def run_tilesweep(args):
         lat.sync()
         ms, _ = lat.kernel_time()
         bpc, cells = lat.traffic_model()
-        rows.append({"tile": "x".join(str(v) for v in tile[:3]) + (" staged" if tile[3] else ""),
+        rows.append({"tile": tile_label(tile),
                      "kernel_ms": ms, "mlups": cells / ms / 1e3,
                      "frac": achieved_gbs(bpc, cells, ms * 1e-3) / peak})
         lat.destroy()

@@ -89,10 +89,15 @@ typedef struct {
     int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 32 x 4;
                                 tile_x a multiple of 32, tile_x * tile_y <= 256 */
     int tile_z;              /* planes per CTA, each thread marching through them; 0 = default 1; <= 64 */
-    int staged;              /* 1: persistent CTAs stage the 27 source rows of each 1-row tile in a
+    int staged;              /* kernel form of the step.  0 = direct loads; with 16-bit storage, the
+                                cumulant collision, single-plane tiles and every nx of the batch even,
+                                the tiles without a no-slip or free-slip face cell then take two cells
+                                of a row per thread (32-bit words, the collision on f32x2 instructions
+                                across the pair; bit for bit the one-cell results).
+                                1 = persistent CTAs stage the 27 source rows of each 1-row tile in a
                                 3-4 stage shared-memory ring filled by TMA bulk copies (needs
-                                tile_y = tile_z = 1 and nx a multiple of 4 (FP32) or 8 (16-bit));
-                                0 = direct loads */
+                                tile_y = tile_z = 1 and nx a multiple of 4 (FP32) or 8 (16-bit)).
+                                2 = direct loads, one cell per thread everywhere */
     int inplace;             /* 1: one PDF array updated in place (AA pattern: even steps pull from the
                                 neighbours and push into the slots they read, odd steps read and write a
                                 cell's own slots), half the PDF memory, for every boundary rule and
@@ -272,9 +277,10 @@ lbm_status lbm_get_diagnostics(lbm_ctx* ctx, double mass_mom[4], long long* at_s
 lbm_status lbm_get_step(lbm_ctx* ctx, long long* step);
 lbm_status lbm_set_step(lbm_ctx* ctx, long long step);
 
-/* CTA tile of the step kernel and the staged mode (see lbm_config.tile_* and
- * staged); changing it rebuilds the work list.  Results do not depend on the
- * tile.  INVALID_ARG for a bad shape. */
+/* CTA tile of the step kernel and its form (see lbm_config.tile_* and staged:
+ * 0 direct, paired cells where they apply; 1 staged rows; 2 direct, one cell
+ * per thread); changing it rebuilds the work list.  Results do not depend on
+ * the tile or the form.  INVALID_ARG for a bad shape or form. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z, int staged);
 lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z, int* staged);
 

@@ -55,6 +55,8 @@ struct Batch {
     int tile_x = 32, tile_y = 4, tile_z = 1;
     int staged = 0;        // rows staged in shared memory by persistent CTAs
     unsigned staged_grid = 0;
+    int single_cell = 0;   // the bulk launch keeps one cell per thread where pairs would apply
+    bool pairs_ok = false; // cumulant collision, 16-bit storage and every nx even: paired bulk cells
     lbm_status status = LBM_OK;
     std::string err;
     bool dirty = true;
@@ -197,8 +199,9 @@ lbm_status validate_cfg(const lbm_config* c, std::string& msg)
         return LBM_ERR_INVALID_ARG;
     }
     if (c->inplace != 0 && c->inplace != 1) { msg = "inplace must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
+    if (c->staged < 0 || c->staged > 2) { msg = "staged must be 0, 1 or 2"; return LBM_ERR_INVALID_ARG; }
     if (c->inplace) {
-        if (tz != 1 || c->staged) {
+        if (tz != 1 || c->staged == 1) {
             msg = "the in-place scheme takes single-plane direct tiles only";
             return LBM_ERR_UNSUPPORTED;
         }
@@ -482,8 +485,9 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
             L.f[1] = h.f[1];
         }
         const bool tiled = b->tile_z == 1;  // k_bulk takes single-plane tiles
+        const bool pairs = tiled && b->pairs_ok && !b->single_cell;
         CK(launch_step(b->coll, b->store, dim3(Np), block, b->stream, ap, false, R + Nf > 0, tiled ? &bp : nullptr,
-                       diag_step));
+                       diag_step, pairs));
     }
     return LBM_OK;
 }
@@ -567,6 +571,10 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     b->staged = 0;
     b->inplace = cfgs[0].inplace;
     const int want_staged = cfgs[0].staged;
+    b->single_cell = want_staged == 2 ? 1 : 0;
+    b->pairs_ok = b->coll == COLL_CUMULANT && b->store != STORE_FP32;
+    for (int i = 0; i < n; ++i)
+        if (cfgs[i].nx % 2 != 0) b->pairs_ok = false;
     b->diag_every = cfgs[0].diag_every;
     b->inst.resize(n);
     lbm_status s = LBM_OK;
@@ -595,7 +603,7 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
         out[i]->idx = i;
         b->refs++;
     }
-    if (want_staged) {
+    if (want_staged == 1) {
         const lbm_status st = lbm_set_tile(out[0], b->tile_x, b->tile_y, b->tile_z, 1);
         if (st != LBM_OK) {
             for (int i = 0; i < n; ++i) lbm_destroy(out[i]);
@@ -1281,12 +1289,13 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z, int st
     if (tile_x < 32 || tile_x % 32 != 0 || tile_y < 1 || tile_x * tile_y > 256 || tile_z < 1 || tile_z > 64)
         return fail(b, LBM_ERR_INVALID_ARG, "tile_x must be a multiple of 32, tile_x * tile_y <= 256, 1 <= tile_z <= 64",
                     false);
-    if (b->inplace && (tile_z != 1 || staged))
+    if (staged < 0 || staged > 2) return fail(b, LBM_ERR_INVALID_ARG, "staged must be 0, 1 or 2", false);
+    if (b->inplace && (tile_z != 1 || staged == 1))
         return fail(b, LBM_ERR_UNSUPPORTED, "the in-place scheme takes single-plane direct tiles only", false);
-    if (staged && !staged_ok(b, tile_y, tile_z))
+    if (staged == 1 && !staged_ok(b, tile_y, tile_z))
         return fail(b, LBM_ERR_INVALID_ARG, "staged rows need tile_y = tile_z = 1 and nx a multiple of 16 bytes", false);
     unsigned grid = 0;
-    if (staged) {
+    if (staged == 1) {
         int dev = 0, sms = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1297,7 +1306,8 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int tile_x, int tile_y, int tile_z, int st
     b->tile_x = tile_x;
     b->tile_y = tile_y;
     b->tile_z = tile_z;
-    b->staged = staged ? 1 : 0;
+    b->staged = staged == 1 ? 1 : 0;
+    b->single_cell = staged == 2 ? 1 : 0;
     b->staged_grid = grid;
     b->dirty = true;
     return sync_descriptors(b);
@@ -1309,7 +1319,7 @@ lbm_status lbm_get_tile(lbm_ctx* ctx, int* tile_x, int* tile_y, int* tile_z, int
     if (tile_x) *tile_x = b->tile_x;
     if (tile_y) *tile_y = b->tile_y;
     if (tile_z) *tile_z = b->tile_z;
-    if (staged) *staged = b->staged;
+    if (staged) *staged = b->staged ? 1 : (b->single_cell ? 2 : 0);
     return LBM_OK;
 }
 
@@ -1408,9 +1418,13 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
         }
     }
     // tile_x, tile_y, tile_z, staged
+    // (staged 2: the single-plane shapes with one cell per thread, where the
+    // bulk would otherwise take two)
     static const int cand[][4] = {{32, 4, 1, 0}, {32, 2, 1, 0}, {32, 8, 1, 0}, {64, 2, 1, 0}, {64, 1, 1, 0},
-                                  {128, 1, 1, 0}, {32, 4, 2, 0}, {32, 4, 4, 0}, {32, 2, 4, 0}, {32, 2, 8, 0},
-                                  {64, 2, 4, 0}, {32, 4, 8, 0}, {64, 1, 1, 1}, {128, 1, 1, 1}, {256, 1, 1, 1}};
+                                  {128, 1, 1, 0}, {64, 4, 1, 0}, {128, 2, 1, 0}, {32, 4, 2, 0}, {32, 4, 4, 0},
+                                  {32, 2, 4, 0}, {32, 2, 8, 0}, {64, 2, 4, 0}, {32, 4, 8, 0}, {32, 4, 1, 2},
+                                  {32, 8, 1, 2}, {64, 2, 1, 2}, {64, 1, 1, 2}, {64, 1, 1, 1}, {128, 1, 1, 1},
+                                  {256, 1, 1, 1}};
     const long long step0 = b->host_step;
     const bool prof = b->profiling;
     Snapshot S;
@@ -1419,7 +1433,8 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
     int best = -1;
     double best_t = 1e300;
     for (int c = 0; s == LBM_OK && c < (int)(sizeof cand / sizeof cand[0]); ++c) {
-        if (cand[c][3] && !staged_ok(b, cand[c][1], cand[c][2])) continue;
+        if (cand[c][3] == 1 && !staged_ok(b, cand[c][1], cand[c][2])) continue;
+        if (cand[c][3] == 2 && !b->pairs_ok) continue;  // the same kernel as staged 0
         s = lbm_set_tile(ctx, cand[c][0], cand[c][1], cand[c][2], cand[c][3]);
         if (s == LBM_ERR_INVALID_ARG || s == LBM_ERR_UNSUPPORTED) {  // does not fit or not built: skip
             s = LBM_OK;
@@ -1455,11 +1470,12 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps_per_candidate, const char* cache
     for (float* p : S.box) dfree(b, p);
     if (s != LBM_OK) return s;
     if (best < 0) return fail(b, LBM_ERR_STATE, "no tile candidate ran");
-    if (tile_out) { tile_out[0] = b->tile_x; tile_out[1] = b->tile_y; tile_out[2] = b->tile_z; tile_out[3] = b->staged; }
+    const int form = b->staged ? 1 : (b->single_cell ? 2 : 0);
+    if (tile_out) { tile_out[0] = b->tile_x; tile_out[1] = b->tile_y; tile_out[2] = b->tile_z; tile_out[3] = form; }
     if (best_ms) *best_ms = best_t;
     if (cache_path)
         if (FILE* fp = std::fopen(cache_path, "a")) {
-            std::fprintf(fp, "%s %d %d %d %d %.9g\n", key.c_str(), b->tile_x, b->tile_y, b->tile_z, b->staged, best_t);
+            std::fprintf(fp, "%s %d %d %d %d %.9g\n", key.c_str(), b->tile_x, b->tile_y, b->tile_z, form, best_t);
             std::fclose(fp);
         }
     return LBM_OK;

@@ -312,47 +312,130 @@ __device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z)
 }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
+// ------------------------------------------------------------------ lane types of the collision
+
+// The cumulant collision is written once for two lane types: float (one cell)
+// and float2 (the cells x and x + 1 of a row, one per lane).  Every operation
+// is explicit and correctly rounded, with no contraction of a product into a
+// sum left to the compiler, and the f32x2 instructions round each lane exactly
+// as the scalar instruction, so a pair of cells evaluated on float2 gives bit
+// for bit the values of the two cells evaluated one at a time on float.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return sub2(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return mul2(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return fma2(a, b, c); }
+__device__ __forceinline__ float2 vneg(float2 a) { return mul2(a, bc2(-1.0f)); }  // exact, signed zeros included
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+template <class V> __device__ __forceinline__ V vc(float c);
+template <> __device__ __forceinline__ float vc<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 vc<float2>(float c) { return bc2(c); }
+
+// The values of the levels c_z = -1 (lo) and c_z = +1 (hi) of a lane type,
+// carried together through the collision's passes: a float2 for one cell, two
+// float2 (each over the two cells) for a pair of cells.
+struct float2x2 {
+    float2 lo, hi;
+};
+template <class V> struct ZPair;
+template <> struct ZPair<float> { using T = float2; };
+template <> struct ZPair<float2> { using T = float2x2; };
+__device__ __forceinline__ float2 zmk(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ float2x2 zmk(float2 lo, float2 hi) { return {lo, hi}; }
+__device__ __forceinline__ float zlo(float2 p) { return p.x; }
+__device__ __forceinline__ float zhi(float2 p) { return p.y; }
+__device__ __forceinline__ float2 zlo(const float2x2& p) { return p.lo; }
+__device__ __forceinline__ float2 zhi(const float2x2& p) { return p.hi; }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return sub2(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return mul2(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return fma2(a, b, c); }
+__device__ __forceinline__ float2x2 padd(const float2x2& a, const float2x2& b) { return {add2(a.lo, b.lo), add2(a.hi, b.hi)}; }
+__device__ __forceinline__ float2x2 psub(const float2x2& a, const float2x2& b) { return {sub2(a.lo, b.lo), sub2(a.hi, b.hi)}; }
+__device__ __forceinline__ float2x2 pmul(const float2x2& a, const float2x2& b) { return {mul2(a.lo, b.lo), mul2(a.hi, b.hi)}; }
+__device__ __forceinline__ float2x2 pfma(const float2x2& a, const float2x2& b, const float2x2& c)
+{
+    return {fma2(a.lo, b.lo, c.lo), fma2(a.hi, b.hi, c.hi)};
+}
+template <class V> __device__ __forceinline__ typename ZPair<V>::T pbc(V v) { return zmk(v, v); }
+
+template <class V>
+struct MomentsV {
+    V drho, jx, jy, jz, Sxx, Syy, Szz, Sxy, Sxz, Syz;
+};
+
 // Raw moments as raw_moments computes them (same operations, same order), with
 // the populations of the planes c_z = -1 and c_z = +1 carried as pairs:
 // hp[3j + i] = (h[3j + i], h[18 + 3j + i]), hs[3j + i] = h[9 + 3j + i].
-__device__ __forceinline__ Moments raw_moments_paired(const float2 hp[9], const float hs[9])
+template <class V>
+__device__ __forceinline__ MomentsV<V> raw_moments_paired(const typename ZPair<V>::T hp[9], const V hs[9])
 {
-    float2 m0p[3], m1p[3], m2p[3];
-    float m0s[3], m1s[3], m2s[3];
+    using P = typename ZPair<V>::T;
+    P m0p[3], m1p[3], m2p[3];
+    V m0s[3], m1s[3], m2s[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        m2p[j] = add2(hp[3 * j + 2], hp[3 * j]);
-        m0p[j] = add2(m2p[j], hp[3 * j + 1]);
-        m1p[j] = sub2(hp[3 * j + 2], hp[3 * j]);
-        m2s[j] = hs[3 * j + 2] + hs[3 * j];
-        m0s[j] = m2s[j] + hs[3 * j + 1];
-        m1s[j] = hs[3 * j + 2] - hs[3 * j];
+        m2p[j] = padd(hp[3 * j + 2], hp[3 * j]);
+        m0p[j] = padd(m2p[j], hp[3 * j + 1]);
+        m1p[j] = psub(hp[3 * j + 2], hp[3 * j]);
+        m2s[j] = vadd(hs[3 * j + 2], hs[3 * j]);
+        m0s[j] = vadd(m2s[j], hs[3 * j + 1]);
+        m1s[j] = vsub(hs[3 * j + 2], hs[3 * j]);
     }
-    // per z level k: pairs hold levels 0 and 2, scalars level 1
-    const float2 A02p = add2(m0p[2], m0p[0]);
-    const float2 A00p = add2(A02p, m0p[1]);
-    const float2 A10p = add2(add2(m1p[0], m1p[1]), m1p[2]);
-    const float2 A20p = add2(add2(m2p[0], m2p[1]), m2p[2]);
-    const float2 A01p = sub2(m0p[2], m0p[0]);
-    const float2 A11p = sub2(m1p[2], m1p[0]);
-    const float A02s = m0s[2] + m0s[0];
-    const float A00s = A02s + m0s[1];
-    const float A10s = m1s[0] + m1s[1] + m1s[2];
-    const float A20s = m2s[0] + m2s[1] + m2s[2];
-    const float A01s = m0s[2] - m0s[0];
-    const float A11s = m1s[2] - m1s[0];
-    Moments M;
-    M.Szz = A00p.y + A00p.x;
-    M.drho = M.Szz + A00s;
-    M.jx = A10p.x + A10s + A10p.y;
-    M.jy = A01p.x + A01s + A01p.y;
-    M.jz = A00p.y - A00p.x;
-    M.Sxx = A20p.x + A20s + A20p.y;
-    M.Syy = A02p.x + A02s + A02p.y;
-    M.Sxy = A11p.x + A11s + A11p.y;
-    M.Sxz = A10p.y - A10p.x;
-    M.Syz = A01p.y - A01p.x;
+    // per z level k: pairs hold levels 0 and 2, the single values level 1
+    const P A02p = padd(m0p[2], m0p[0]);
+    const P A00p = padd(A02p, m0p[1]);
+    const P A10p = padd(padd(m1p[0], m1p[1]), m1p[2]);
+    const P A20p = padd(padd(m2p[0], m2p[1]), m2p[2]);
+    const P A01p = psub(m0p[2], m0p[0]);
+    const P A11p = psub(m1p[2], m1p[0]);
+    const V A02s = vadd(m0s[2], m0s[0]);
+    const V A00s = vadd(A02s, m0s[1]);
+    const V A10s = vadd(vadd(m1s[0], m1s[1]), m1s[2]);
+    const V A20s = vadd(vadd(m2s[0], m2s[1]), m2s[2]);
+    const V A01s = vsub(m0s[2], m0s[0]);
+    const V A11s = vsub(m1s[2], m1s[0]);
+    MomentsV<V> M;
+    M.Szz = vadd(zhi(A00p), zlo(A00p));
+    M.drho = vadd(M.Szz, A00s);
+    M.jx = vadd(vadd(zlo(A10p), A10s), zhi(A10p));
+    M.jy = vadd(vadd(zlo(A01p), A01s), zhi(A01p));
+    M.jz = vsub(zhi(A00p), zlo(A00p));
+    M.Sxx = vadd(vadd(zlo(A20p), A20s), zhi(A20p));
+    M.Syy = vadd(vadd(zlo(A02p), A02s), zhi(A02p));
+    M.Sxy = vadd(vadd(zlo(A11p), A11s), zhi(A11p));
+    M.Sxz = vsub(zhi(A10p), zlo(A10p));
+    M.Syz = vsub(zhi(A01p), zlo(A01p));
     return M;
+}
+
+// The one-dimensional map of the passes (see Axis) on a lane type.
+template <class V>
+struct AxisV {
+    V dm, dp, u2, bm, bp;
+};
+template <class V>
+__device__ __forceinline__ AxisV<V> axis_of_v(V u)
+{
+    AxisV<V> a;
+    a.u2 = vmul(u, u);
+    a.dm = vmul(vc<V>(0.5f), vsub(a.u2, u));
+    a.dp = vmul(vc<V>(0.5f), vadd(a.u2, u));
+    a.bm = vsub(u, vc<V>(0.5f));
+    a.bp = vadd(u, vc<V>(0.5f));
+    return a;
+}
+template <class V>
+__device__ __forceinline__ void inv_full_v(const AxisV<V>& a, V k0, V k1, V h2, V& fm, V& f0, V& fp)
+{
+    fm = vfma(a.dm, k0, vfma(a.bm, k1, h2));
+    fp = vfma(a.dp, k0, vfma(a.bp, k1, h2));
+    f0 = vsub(vsub(k0, fm), fp);
 }
 
 // Cumulant collision with shear rate omega, bulk and all higher-order rates 1
@@ -373,88 +456,96 @@ __device__ __forceinline__ Moments raw_moments_paired(const float2 hp[9], const 
 // (moment (a, b, c) scaled by 2^-(number of indices equal to 2)), so that every
 // pass receives h2 = k2/2 directly.
 //
-// The values of the z levels c_z = -1 and +1 travel as FP32 pairs through all
+// The values of the z levels c_z = -1 and +1 travel as pairs through all
 // three passes: the z pass produces them together (its f(-1), f(+1)), and the
 // y and x passes treat the two levels alike (their weights are even in c_z), so
-// those passes run on f32x2 instructions for two thirds of their columns.
-__device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy, float Fz, float omega, float& drho_o,
-                                                 float& jx_o, float& jy_o, float& jz_o)
+// for one cell those passes run on f32x2 instructions for two thirds of their
+// columns.  V = float2 evaluates two cells on f32x2 instructions throughout.
+template <class V>
+__device__ __forceinline__ void collide_cumulant_v(V h[27], V Fx, V Fy, V Fz, float omega, V& drho_o, V& jx_o,
+                                                   V& jy_o, V& jz_o)
 {
-    float2 hp[9];
-    float hs[9];
+    using P = typename ZPair<V>::T;
+    P hp[9];
+    V hs[9];
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
-        hp[r] = make_float2(h[r], h[18 + r]);
+        hp[r] = zmk(h[r], h[18 + r]);
         hs[r] = h[9 + r];
     }
-    const Moments M = raw_moments_paired(hp, hs);
-    const float rho = 1.0f + M.drho;
+    const MomentsV<V> M = raw_moments_paired<V>(hp, hs);
+    const V rho = vadd(vc<V>(1.0f), M.drho);
     // correctly rounded: the equilibrium momentum rho (j + F/2)/rho must not
     // carry a one-signed reciprocal error, or the lattice momentum drifts
-    const float inv = __frcp_rn(rho);
-    const float hFx = 0.5f * Fx, hFy = 0.5f * Fy, hFz = 0.5f * Fz;
-    const float ux = (M.jx + hFx) * inv;
-    const float uy = (M.jy + hFy) * inv;
-    const float uz = (M.jz + hFz) * inv;
+    const V inv = vrcp(rho);
+    const V hFx = vmul(vc<V>(0.5f), Fx), hFy = vmul(vc<V>(0.5f), Fy), hFz = vmul(vc<V>(0.5f), Fz);
+    const V ux = vmul(vadd(M.jx, hFx), inv);
+    const V uy = vmul(vadd(M.jy, hFy), inv);
+    const V uz = vmul(vadd(M.jz, hFz), inv);
     const float third = 1.0f / 3.0f;
     // second central moments minus rho/3 delta, using rho u = j + F/2:
     //   S_ab - rho u_a u_b + (u_a F_b + u_b F_a)/2 = S_ab - j_a u_b + u_a F_b/2
-    const float t3 = M.drho * third;
-    const float axx = fmaf(ux, hFx - M.jx, M.Sxx - t3);
-    const float ayy = fmaf(uy, hFy - M.jy, M.Syy - t3);
-    const float azz = fmaf(uz, hFz - M.jz, M.Szz - t3);
-    const float axy = fmaf(-M.jx, uy, fmaf(ux, hFy, M.Sxy));
-    const float axz = fmaf(-M.jx, uz, fmaf(ux, hFz, M.Sxz));
-    const float ayz = fmaf(-M.jy, uz, fmaf(uy, hFz, M.Syz));
-    const float om1 = 1.0f - omega;
-    const float tr3 = (axx + ayy + azz) * third;
-    const float bxx = om1 * (axx - tr3), byy = om1 * (ayy - tr3), bzz = om1 * (azz - tr3);
-    const float bxy = om1 * axy, bxz = om1 * axz, byz = om1 * ayz;
-    const float inv2 = 0.5f * inv, inv4 = 0.25f * inv;
-    const float b2xy = 2.0f * bxy, b2xz = 2.0f * bxz, b2yz = 2.0f * byz;
+    const V axx = vfma(ux, vsub(hFx, M.jx), vfma(M.drho, vc<V>(-third), M.Sxx));
+    const V ayy = vfma(uy, vsub(hFy, M.jy), vfma(M.drho, vc<V>(-third), M.Syy));
+    const V azz = vfma(uz, vsub(hFz, M.jz), vfma(M.drho, vc<V>(-third), M.Szz));
+    const V njx = vneg(M.jx), njy = vneg(M.jy);
+    const V axy = vfma(njx, uy, vfma(ux, hFy, M.Sxy));
+    const V axz = vfma(njx, uz, vfma(ux, hFz, M.Sxz));
+    const V ayz = vfma(njy, uz, vfma(uy, hFz, M.Syz));
+    const V om1 = vc<V>(1.0f - omega);
+    const V tr = vadd(vadd(axx, ayy), azz);
+    const V bxx = vmul(om1, vfma(tr, vc<V>(-third), axx));
+    const V byy = vmul(om1, vfma(tr, vc<V>(-third), ayy));
+    const V bzz = vmul(om1, vfma(tr, vc<V>(-third), azz));
+    const V bxy = vmul(om1, axy), bxz = vmul(om1, axz), byz = vmul(om1, ayz);
+    const V inv2 = vmul(vc<V>(0.5f), inv), inv4 = vmul(vc<V>(0.25f), inv);
+    const V b2xy = vadd(bxy, bxy), b2xz = vadd(bxz, bxz), b2yz = vadd(byz, byz);
     // collided deviations in the halved basis: orders 4 and 6 are the Gaussian
     // (Isserlis) products of the collided second-order moments minus those of
     // the equilibrium, expanded so that no equilibrium-sized term cancels
-    const float d200 = 0.5f * bxx, d020 = 0.5f * byy, d002 = 0.5f * bzz;
-    const float d220 = fmaf(bxx + byy, 1.0f / 12.0f, fmaf(bxx, byy, bxy * b2xy) * inv4);
-    const float d202 = fmaf(bxx + bzz, 1.0f / 12.0f, fmaf(bxx, bzz, bxz * b2xz) * inv4);
-    const float d022 = fmaf(byy + bzz, 1.0f / 12.0f, fmaf(byy, bzz, byz * b2yz) * inv4);
-    const float d211 = fmaf(byz, 1.0f / 6.0f, fmaf(bxx, byz, bxy * b2xz) * inv2);
-    const float d121 = fmaf(bxz, 1.0f / 6.0f, fmaf(byy, bxz, bxy * b2yz) * inv2);
-    const float d112 = fmaf(bxy, 1.0f / 6.0f, fmaf(bzz, bxy, bxz * b2yz) * inv2);
-    float d222;
+    const V d200 = vmul(vc<V>(0.5f), bxx), d020 = vmul(vc<V>(0.5f), byy), d002 = vmul(vc<V>(0.5f), bzz);
+    const V c12 = vc<V>(1.0f / 12.0f), c6 = vc<V>(1.0f / 6.0f);
+    const V d220 = vfma(vadd(bxx, byy), c12, vmul(vfma(bxx, byy, vmul(bxy, b2xy)), inv4));
+    const V d202 = vfma(vadd(bxx, bzz), c12, vmul(vfma(bxx, bzz, vmul(bxz, b2xz)), inv4));
+    const V d022 = vfma(vadd(byy, bzz), c12, vmul(vfma(byy, bzz, vmul(byz, b2yz)), inv4));
+    const V d211 = vfma(byz, c6, vmul(vfma(bxx, byz, vmul(bxy, b2xz)), inv2));
+    const V d121 = vfma(bxz, c6, vmul(vfma(byy, bxz, vmul(bxy, b2yz)), inv2));
+    const V d112 = vfma(bxy, c6, vmul(vfma(bzz, bxy, vmul(bxz, b2yz)), inv2));
+    V d222;
     {
         // g = s_xx s_yy s_zz-type product of (1/3 + s) minus 1/27, plus the
         // off-diagonal pairings, with s = b / rho
-        const float sxx = bxx * inv, syy = byy * inv, szz = bzz * inv;
-        const float sxy = bxy * inv, sxz = bxz * inv, syz = byz * inv;
-        const float p = sxx + syy, q = sxx * syy;
-        const float diag = fmaf(p + szz, 1.0f / 9.0f, fmaf(fmaf(szz, p, q), third, q * szz));
-        const float pair = fmaf(third + sxx, syz * syz, fmaf(third + syy, sxz * sxz, (third + szz) * (sxy * sxy)));
-        const float g = fmaf(2.0f, pair, fmaf(8.0f * sxy, sxz * syz, diag));
-        d222 = (0.125f * rho) * g;
+        const V sxx = vmul(bxx, inv), syy = vmul(byy, inv), szz = vmul(bzz, inv);
+        const V sxy = vmul(bxy, inv), sxz = vmul(bxz, inv), syz = vmul(byz, inv);
+        const V p = vadd(sxx, syy), q = vmul(sxx, syy);
+        const V t = vc<V>(third);
+        const V diag = vfma(vadd(p, szz), vc<V>(1.0f / 9.0f), vfma(vfma(szz, p, q), t, vmul(q, szz)));
+        const V pair = vfma(vadd(t, sxx), vmul(syz, syz),
+                            vfma(vadd(t, syy), vmul(sxz, sxz), vmul(vadd(t, szz), vmul(sxy, sxy))));
+        const V g = vfma(vc<V>(2.0f), pair, vfma(vmul(vc<V>(8.0f), sxy), vmul(sxz, syz), diag));
+        d222 = vmul(vmul(vc<V>(0.125f), rho), g);
     }
-    const Axis X = axis_of(ux), Y = axis_of(uy), Z = axis_of(uz);
+    const AxisV<V> X = axis_of_v(ux), Y = axis_of_v(uy), Z = axis_of_v(uz);
     // z pass over the columns (a, b): the pair (f(-1), f(+1)) = Gp[3b + a] and
     // f(0) = Gs[3b + a]; the map's coefficients enter as pairs (dm, dp), (bm, bp)
-    const float2 zd = make_float2(Z.dm, Z.dp), zb = make_float2(Z.bm, Z.bp);
-    float2 Gp[9];
-    float Gs[9];
-    auto z_k1h2 = [&](int c, float k1, float h2) {
-        Gp[c] = fma2(zb, bc2(k1), bc2(h2));
-        Gs[c] = -Gp[c].x - Gp[c].y;
+    const P zd = zmk(Z.dm, Z.dp), zb = zmk(Z.bm, Z.bp);
+    P Gp[9];
+    V Gs[9];
+    auto z_k1h2 = [&](int c, V k1, V h2) {
+        Gp[c] = pfma(zb, pbc(k1), pbc(h2));
+        Gs[c] = vsub(vneg(zlo(Gp[c])), zhi(Gp[c]));
     };
-    auto z_k0k1 = [&](int c, float k0, float k1) {
-        Gp[c] = fma2(zd, bc2(k0), mul2(zb, bc2(k1)));
-        Gs[c] = k0 - Gp[c].x - Gp[c].y;
+    auto z_k0k1 = [&](int c, V k0, V k1) {
+        Gp[c] = pfma(zd, pbc(k0), pmul(zb, pbc(k1)));
+        Gs[c] = vsub(vsub(k0, zlo(Gp[c])), zhi(Gp[c]));
     };
-    auto z_k0h2 = [&](int c, float k0, float h2) {
-        Gp[c] = fma2(zd, bc2(k0), bc2(h2));
-        Gs[c] = k0 - Gp[c].x - Gp[c].y;
+    auto z_k0h2 = [&](int c, V k0, V h2) {
+        Gp[c] = pfma(zd, pbc(k0), pbc(h2));
+        Gs[c] = vsub(vsub(k0, zlo(Gp[c])), zhi(Gp[c]));
     };
-    auto z_k1 = [&](int c, float k1) {
-        Gp[c] = mul2(zb, bc2(k1));
-        Gs[c] = -Gp[c].x - Gp[c].y;
+    auto z_k1 = [&](int c, V k1) {
+        Gp[c] = pmul(zb, pbc(k1));
+        Gs[c] = vsub(vneg(zlo(Gp[c])), zhi(Gp[c]));
     };
     z_k1h2(0, hFz, d002);
     z_k0k1(1, hFx, bxz);
@@ -468,65 +559,72 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
     {
         // equilibrium part of the z pass: rho phi_z - w1 on the columns (0, 0),
         // (2, 0), (0, 2), (2, 2) with the weights 1, 1/6, 1/6, 1/36
-        const float2 gzp = fma2(bc2(M.drho), add2(bc2(w1(1)), zd), zd);  // w1(-1) = w1(+1)
-        Gp[0] = add2(Gp[0], gzp);
-        Gp[2] = fma2(bc2(1.0f / 6.0f), gzp, Gp[2]);
-        Gp[6] = fma2(bc2(1.0f / 6.0f), gzp, Gp[6]);
-        Gp[8] = fma2(bc2(1.0f / 36.0f), gzp, Gp[8]);
-        const float dz = -Z.u2;
-        const float gz = fmaf(M.drho, w1(0) + dz, dz);
-        Gs[0] += gz;
-        Gs[2] = fmaf(1.0f / 6.0f, gz, Gs[2]);
-        Gs[6] = fmaf(1.0f / 6.0f, gz, Gs[6]);
-        Gs[8] = fmaf(1.0f / 36.0f, gz, Gs[8]);
+        const P gzp = pfma(pbc(M.drho), padd(pbc(vc<V>(w1(1))), zd), zd);  // w1(-1) = w1(+1)
+        Gp[0] = padd(Gp[0], gzp);
+        Gp[2] = pfma(pbc(vc<V>(1.0f / 6.0f)), gzp, Gp[2]);
+        Gp[6] = pfma(pbc(vc<V>(1.0f / 6.0f)), gzp, Gp[6]);
+        Gp[8] = pfma(pbc(vc<V>(1.0f / 36.0f)), gzp, Gp[8]);
+        const V dz = vneg(Z.u2);
+        const V gz = vfma(M.drho, vadd(vc<V>(w1(0)), dz), dz);
+        Gs[0] = vadd(Gs[0], gz);
+        Gs[2] = vfma(vc<V>(1.0f / 6.0f), gz, Gs[2]);
+        Gs[6] = vfma(vc<V>(1.0f / 6.0f), gz, Gs[6]);
+        Gs[8] = vfma(vc<V>(1.0f / 36.0f), gz, Gs[8]);
     }
     // y pass over the columns (a, k); the equilibrium part e0_a w1 dphi_y enters
     // as the moments (0, u_y, -u_y^2), which the map takes to dphi_y
-    const float2 ydm = bc2(Y.dm), ydp = bc2(Y.dp), ybm = bc2(Y.bm), ybp = bc2(Y.bp);
+    const P ydm = pbc(Y.dm), ydp = pbc(Y.dp), ybm = pbc(Y.bm), ybp = pbc(Y.bp);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float2 k1p = Gp[3 + a], h2p = Gp[6 + a];
-        float k1s = Gs[3 + a], h2s = Gs[6 + a];
+        P k1p = Gp[3 + a], h2p = Gp[6 + a];
+        V k1s = Gs[3 + a], h2s = Gs[6 + a];
         if (a != 1) {
             const float ea = a == 0 ? 1.0f : 1.0f / 6.0f;
             const float ep = ea * w1(1), es = ea * w1(0);  // w1(-1) = w1(+1)
-            k1p = fma2(bc2(ep), bc2(uy), k1p);
-            h2p = fma2(bc2(-0.5f * ep), bc2(Y.u2), h2p);
-            k1s = fmaf(es, uy, k1s);
-            h2s = fmaf(-0.5f * es, Y.u2, h2s);
+            k1p = pfma(pbc(vc<V>(ep)), pbc(uy), k1p);
+            h2p = pfma(pbc(vc<V>(-0.5f * ep)), pbc(Y.u2), h2p);
+            k1s = vfma(vc<V>(es), uy, k1s);
+            h2s = vfma(vc<V>(-0.5f * es), Y.u2, h2s);
         }
-        const float2 k0p = Gp[a];
-        const float2 fm = fma2(ydm, k0p, fma2(ybm, k1p, h2p));
-        const float2 fp = fma2(ydp, k0p, fma2(ybp, k1p, h2p));
+        const P k0p = Gp[a];
+        const P fm = pfma(ydm, k0p, pfma(ybm, k1p, h2p));
+        const P fp = pfma(ydp, k0p, pfma(ybp, k1p, h2p));
         Gp[a] = fm;
-        Gp[3 + a] = sub2(sub2(k0p, fm), fp);
+        Gp[3 + a] = psub(psub(k0p, fm), fp);
         Gp[6 + a] = fp;
-        inv_full(Y, Gs[a], k1s, h2s, Gs[a], Gs[3 + a], Gs[6 + a]);
+        inv_full_v(Y, Gs[a], k1s, h2s, Gs[a], Gs[3 + a], Gs[6 + a]);
     }
     // x pass over the rows (j, k), with w1 w1 dphi_x entered the same way
-    const float2 xdm = bc2(X.dm), xdp = bc2(X.dp), xbm = bc2(X.bm), xbp = bc2(X.bp);
+    const P xdm = pbc(X.dm), xdp = pbc(X.dp), xbm = pbc(X.bm), xbp = pbc(X.bp);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float ep = w2(j - 1, 1), es = w2(j - 1, 0);  // w2(j, -1) = w2(j, +1)
-        const float2 k1p = fma2(bc2(ep), bc2(ux), Gp[3 * j + 1]);
-        const float2 h2p = fma2(bc2(-0.5f * ep), bc2(X.u2), Gp[3 * j + 2]);
-        const float2 k0p = Gp[3 * j];
-        const float2 fm = fma2(xdm, k0p, fma2(xbm, k1p, h2p));
-        const float2 fp = fma2(xdp, k0p, fma2(xbp, k1p, h2p));
-        const float2 f0 = sub2(sub2(k0p, fm), fp);
-        h[3 * j] = fm.x;
-        h[3 * j + 1] = f0.x;
-        h[3 * j + 2] = fp.x;
-        h[18 + 3 * j] = fm.y;
-        h[18 + 3 * j + 1] = f0.y;
-        h[18 + 3 * j + 2] = fp.y;
-        const float k1s = fmaf(es, ux, Gs[3 * j + 1]), h2s = fmaf(-0.5f * es, X.u2, Gs[3 * j + 2]);
-        inv_full(X, Gs[3 * j], k1s, h2s, h[9 + 3 * j], h[9 + 3 * j + 1], h[9 + 3 * j + 2]);
+        const P k1p = pfma(pbc(vc<V>(ep)), pbc(ux), Gp[3 * j + 1]);
+        const P h2p = pfma(pbc(vc<V>(-0.5f * ep)), pbc(X.u2), Gp[3 * j + 2]);
+        const P k0p = Gp[3 * j];
+        const P fm = pfma(xdm, k0p, pfma(xbm, k1p, h2p));
+        const P fp = pfma(xdp, k0p, pfma(xbp, k1p, h2p));
+        const P f0 = psub(psub(k0p, fm), fp);
+        h[3 * j] = zlo(fm);
+        h[3 * j + 1] = zlo(f0);
+        h[3 * j + 2] = zlo(fp);
+        h[18 + 3 * j] = zhi(fm);
+        h[18 + 3 * j + 1] = zhi(f0);
+        h[18 + 3 * j + 2] = zhi(fp);
+        const V k1s = vfma(vc<V>(es), ux, Gs[3 * j + 1]), h2s = vfma(vc<V>(-0.5f * es), X.u2, Gs[3 * j + 2]);
+        inv_full_v(X, Gs[3 * j], k1s, h2s, h[9 + 3 * j], h[9 + 3 * j + 1], h[9 + 3 * j + 2]);
     }
     drho_o = M.drho;
-    jx_o = M.jx + Fx;
-    jy_o = M.jy + Fy;
-    jz_o = M.jz + Fz;
+    jx_o = vadd(M.jx, Fx);
+    jy_o = vadd(M.jy, Fy);
+    jz_o = vadd(M.jz, Fz);
+}
+
+// One cell (the form every kernel but the paired bulk kernel uses).
+__device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy, float Fz, float omega, float& drho_o,
+                                                 float& jx_o, float& jy_o, float& jz_o)
+{
+    collide_cumulant_v<float>(h, Fx, Fy, Fz, omega, drho_o, jx_o, jy_o, jz_o);
 }
 
 // BGK toward the polynomial equilibrium with a Smagorinsky eddy viscosity
@@ -1387,6 +1485,139 @@ __global__ void __launch_bounds__(256, 4) k_bulk(const StepArgs A, const BulkPar
         const unsigned cell = ((unsigned)z * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
 #pragma unroll
         for (int q = 0; q < 27; ++q) Io<T>::st(dst + ((unsigned)q * uN + cell), h[q]);
+    }
+    if (DIAG) diag_close(A, A.dom + inst, step, o_m, o_jx, o_jy, o_jz, s_red);
+    if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Two cells of a row per thread, for 16-bit storage: the cells x and x + 1
+// (x even) share one 32-bit word of every PDF plane they store, and their
+// pulled values come from 32-bit words too: c_x = 0 from the pair's own word,
+// c_x = -1 from its own and the right neighbour's, c_x = +1 from the left
+// neighbour's and its own.  The collision runs on f32x2 instructions across the
+// two cells (collide_cumulant_v<float2>), bit for bit the one-cell evaluation,
+// and each store packs the pair with one conversion.  Half the threads of
+// k_bulk, each with two cells' work and about half the instructions per cell;
+// nx must be even (rows and planes then start on 32-bit words).  The launch's
+// block is (tile_x / 2, tile_y).
+template <typename T>
+struct Pack16;
+template <>
+struct Pack16<__nv_bfloat16> {
+    static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __uint_as_float(w & 0xFFFF0000u); }
+    static __device__ __forceinline__ unsigned pack(float a, float b)
+    {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);  // a at the lower address
+        return *reinterpret_cast<const unsigned*>(&v);
+    }
+};
+template <>
+struct Pack16<__half> {
+    static __device__ __forceinline__ float lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    static __device__ __forceinline__ unsigned pack(float a, float b)
+    {
+        const __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const unsigned*>(&v);
+    }
+};
+__device__ __forceinline__ unsigned ld_word(const unsigned* p)
+{
+    unsigned v;
+    asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+template <typename T, bool DIAG, bool SINGLE>
+__global__ void __launch_bounds__(128, 4) k_bulk2(const StepArgs A, const BulkParams P)
+{
+    static_assert(sizeof(T) == 2, "paired cells are for 16-bit storage");
+    using W = Pack16<T>;
+    __shared__ double s_red[DIAG ? 8 : 1][4];
+    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
+    const int inst = SINGLE ? 0 : tile_lattice(tile);
+    const LatHot& L = P.lat[inst];
+    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
+    const int x0 = (int)(tile & 0xFFFF);
+    const int x = x0 + 2 * (int)threadIdx.x;  // cells x, x + 1
+    const long long step = __ldcg(A.step_slot + A.parity);
+    if (A.write_step && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        A.step_slot[A.parity ^ 1] = step + 1;
+        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
+    double o_m = 0.0, o_jx = 0.0, o_jy = 0.0, o_jz = 0.0;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    if (x < nx && y < ny) {
+        const unsigned* __restrict__ src = (const unsigned*)L.f[A.parity];
+        unsigned* __restrict__ dst = (unsigned*)L.f[A.parity ^ 1];
+        const unsigned N2 = L.N >> 1;  // words per plane
+        int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+        if (ym < 0) ym += ny; if (yp >= ny) yp -= ny;
+        if (zm < 0) zm += nz; if (zp >= nz) zp -= nz;
+        const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+        const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+        const unsigned nx2 = (unsigned)nx >> 1, nxy2 = nx2 * (unsigned)ny;
+        const unsigned xw = (unsigned)x >> 1;
+        float2 h[27];
+        // words of the left pair (x - 2, x - 1) and right pair (x + 2, x + 3),
+        // relative to the pair's own: in tiles clear of both x faces (uniform over
+        // the CTA) -1 and +1; at the faces wrapped (periodic x) or, with an inlet
+        // and outlet, the pair's own word (the inlet replaces the x = 0 cell's
+        // c_x = +1 values below; at the outlet the last cell's c_x = -1 source is
+        // the clamped cell x + 1 itself, the high half of its own word)
+        int dl = -1, dr = 1;
+        bool clamp_r = false;
+        if (!(x0 > 0 && x0 + 2 * (int)blockDim.x < nx)) {
+            if (x == 0) dl = L.inout ? 0 : (int)nx2 - 1;
+            if (x + 2 == nx) {
+                dr = L.inout ? 0 : -((int)nx2 - 1);
+                clamp_r = L.inout != 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned* zr = src + zs[k] * nxy2;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const unsigned* r = zr + (ys[j] * nx2 + xw);
+                const int q = k * 9 + j * 3;
+                const unsigned* p0 = r + (size_t)q * N2;         // c_x = -1: sources x + 1, x + 2
+                const unsigned* p1 = r + (size_t)(q + 1) * N2;   // c_x = 0
+                const unsigned* p2 = r + (size_t)(q + 2) * N2;   // c_x = +1: sources x - 1, x
+                const unsigned o0 = ld_word(p0), r0 = ld_word(p0 + dr);
+                const unsigned o1 = ld_word(p1);
+                const unsigned l2 = ld_word(p2 + dl), o2 = ld_word(p2);
+                h[q] = make_float2(W::hi(o0), clamp_r ? W::hi(r0) : W::lo(r0));
+                h[q + 1] = make_float2(W::lo(o1), W::hi(o1));
+                h[q + 2] = make_float2(W::hi(l2), W::lo(o2));
+            }
+        }
+        if (L.inout && x == 0) {
+            // the x = 0 cell's nine directions with c_x = +1 across the inlet face,
+            // from the ghost columns (y - c_y, z - c_z); then this column's ghosts
+            // for step n+1
+            const DevDomain* D = A.dom + inst;
+            const float* gb = D->inflow_ghost[step & 1];
+            const int plane = ny * nz;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) h[k * 9 + j * 3 + 2].x = gb[(k * 3 + j) * plane + (int)zs[k] * ny + (int)ys[j]];
+            write_inlet_ghost(D, step + 1, y, z);
+        }
+        float2 m, jx, jy, jz;
+        collide_cumulant_v<float2>(h, bc2(L.body[0]), bc2(L.body[1]), bc2(L.body[2]), L.omega, m, jx, jy, jz);
+        if (DIAG) {
+            o_m = (double)m.x + (double)m.y;
+            o_jx = (double)jx.x + (double)jx.y;
+            o_jy = (double)jy.x + (double)jy.y;
+            o_jz = (double)jz.x + (double)jz.y;
+        }
+        unsigned* c = dst + (((unsigned)z * (unsigned)ny + (unsigned)y) * nx2 + xw);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) c[(size_t)q * N2] = W::pack(h[q].x, h[q].y);
     }
     if (DIAG) diag_close(A, A.dom + inst, step, o_m, o_jx, o_jy, o_jz, s_red);
     if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -2269,8 +2500,25 @@ static cudaError_t launch_dependent_bulk(void (*kernel)(StepArgs, BulkParams), d
     return cudaLaunchKernelEx(&cfg, kernel, a, p);
 }
 
+// The paired bulk kernel for a collision and storage (the cumulant collision
+// with 16-bit storage); false where it is not built.
+template <int C, typename T>
+static bool paired_form(void (*&kb)(StepArgs, BulkParams), bool diag, bool single)
+{
+    if constexpr (C == COLL_CUMULANT && sizeof(T) == 2) {
+        kb = diag ? (single ? k_bulk2<T, true, true> : k_bulk2<T, true, false>)
+                  : (single ? k_bulk2<T, false, true> : k_bulk2<T, false, false>);
+        return true;
+    } else {
+        (void)kb;
+        (void)diag;
+        (void)single;
+        return false;
+    }
+}
+
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
-                        bool dependent, const BulkParams* bulk, bool diag_step)
+                        bool dependent, const BulkParams* bulk, bool diag_step, bool pairs)
 {
     const bool march = a.tile_z > 1;
 #define LBM_STEP_CASE(C, S, T)                                                                        \
@@ -2291,8 +2539,13 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
             void (*kb)(StepArgs, BulkParams) =                                                        \
                 diag_step ? (a.n_inst == 1 ? k_bulk<C, T, true, true> : k_bulk<C, T, true, false>)    \
                           : (a.n_inst == 1 ? k_bulk<C, T, false, true> : k_bulk<C, T, false, false>); \
-            if (dependent) return launch_dependent_bulk(kb, grid, block, s, a, *bulk);                \
-            kb<<<grid, block, 0, s>>>(a, *bulk);                                                      \
+            dim3 blk = block;                                                                         \
+            if (pairs) {                                                                              \
+                if (!paired_form<C, T>(kb, diag_step, a.n_inst == 1)) return cudaErrorInvalidValue;  \
+                blk.x = block.x / 2;                                                                  \
+            }                                                                                         \
+            if (dependent) return launch_dependent_bulk(kb, grid, blk, s, a, *bulk);                  \
+            kb<<<grid, blk, 0, s>>>(a, *bulk);                                                        \
         }                                                                                             \
         return cudaGetLastError();                                                                    \
     }

@@ -28,6 +28,7 @@ def _create(**kw):
     dict(bc=(7, 0, 0)), dict(nx=1, bc=("inout", "periodic", "periodic")),
     dict(diag_every=-1),
     dict(tile=(16, 4)), dict(tile=(48, 2)), dict(tile=(64, 8)), dict(tile=(32, 2, 65)), dict(tile=(32, -1)),
+    dict(tile=(32, 4, 1, 3)), dict(tile=(32, 4, 1, -1)),
 ])
 def test_invalid_configurations_are_rejected_on_the_host(kw):
     assert _create(**kw) == INVALID_ARG
