@@ -334,7 +334,7 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches);
  * call may wait for earlier work on that stream before it returns; the
  * outputs are complete once the stream has passed the call's work.  Nothing
  * is allocated: the scratch is one static
- * device block of about 300 KB that every GPU loading this library holds
+ * device block of about 180 KB that every GPU loading this library holds
  * until the process exits.  Limits: at most 1024 elements and 8192 polar
  * points (INVALID_ARG beyond, before anything is enqueued).  The first call
  * on a device looks up the block's address (make it before any stream

@@ -267,10 +267,9 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
     I.d_turb = (DevTurbine*)dalloc(b, sizeof(DevTurbine) * kMaxTurbines);
     void* ep = dalloc(b, sizeof(float4) * kMaxElements * 4);
     void* el = dalloc(b, sizeof(double) * 2 * kMaxElements);
-    void* ec = dalloc(b, sizeof(float4) * 8 * kMaxElements);
     void* ld = dalloc(b, sizeof(double) * 4 * kMaxTurbines);
     I.small = (unsigned char*)dalloc(b, 256);
-    if (!I.d_turb || !ep || !el || !ec || !ld || !I.small) return fail(b, LBM_ERR_OOM, "descriptor allocation failed");
+    if (!I.d_turb || !ep || !el || !ld || !I.small) return fail(b, LBM_ERR_OOM, "descriptor allocation failed");
     CK(cudaMemsetAsync(ep, 0, sizeof(float4) * kMaxElements * 4, b->stream));
     CK(cudaMemsetAsync(el, 0, sizeof(double) * 2 * kMaxElements, b->stream));
     CK(cudaMemsetAsync(ld, 0, sizeof(double) * 4 * kMaxTurbines, b->stream));
@@ -281,7 +280,6 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
     h.el_force[0] = e4 + 2 * kMaxElements;
     h.el_force[1] = e4 + 3 * kMaxElements;
     h.el_load = (double*)el;
-    h.el_corner = (float4*)ec;
     h.loads[0] = (double*)ld;
     h.loads[1] = (double*)ld + 2 * kMaxTurbines;
     h.diag_acc = (double*)I.small;             // 4 doubles
@@ -291,7 +289,6 @@ lbm_status init_instance(Batch* b, Instance& I, const lbm_config& c)
     h.turb = I.d_turb;
     h.n_turb = 0;
     h.n_el = 0;
-    h.n_rotor_tiles = 0;
     h.diag_every = c.diag_every;
     return LBM_OK;
 }
@@ -338,7 +335,6 @@ lbm_status sync_descriptors(Batch* b)
                 }
             }
         // z-major order (x fastest), as the bulk streams plane after plane
-        int nrot = 0;
         for (int k = 0; k < nzb; ++k)
             for (int j = 0; j < nyb; ++j)
                 for (int l = 0; l < nxb; ++l) {
@@ -357,10 +353,8 @@ lbm_status sync_descriptors(Batch* b)
                     } else if (p > 0) {
                         rotor.push_back(pack_tile((int)i, z, y0, x0, true, p));
                         rotor_planes = std::max(rotor_planes, p);
-                        ++nrot;
                     }
                 }
-        I.h.n_rotor_tiles = nrot;
         std::vector<DevTurbine> dt;
         for (auto& t : I.turb) dt.push_back(t.dev);
         if (!dt.empty())
@@ -425,10 +419,30 @@ cudaError_t write_step_slot(Batch* b)
     return e;
 }
 
-// One time step.  Staged rows: one persistent launch over the whole work list.
-// Otherwise two launches (k_step or, in place, k_step_aa): the rotor tiles
-// (first in the list), then the rest, allowed to overlap the rotor launch;
-// the step counter is advanced by the second (or by the only one).
+// Arguments of the actuator-line launch over every lattice with blade
+// elements: of step n+1 inside the time step n (step read from the device slot
+// `slot`, the array and layout the step leaves), or of the step `step` on the
+// current array (refresh after a state change).
+AlmArgs alm_args(Batch* b, const long long* step_slot, int slot, long long step, int array, int swapped)
+{
+    AlmArgs a{};
+    a.dom = b->d_dom;
+    int n_el[kMaxInstances];
+    for (size_t i = 0; i < b->inst.size(); ++i) n_el[i] = b->inst[i].h.n_el;
+    alm_blocks(a, n_el, (int)b->inst.size());
+    a.step_slot = step_slot;
+    a.slot = slot;
+    a.step = step;
+    a.array = array;
+    a.swapped = swapped;
+    return a;
+}
+
+// One time step.  Staged rows: one persistent launch over the whole work list,
+// then (with rotors) the actuator line of the next step.  Otherwise (k_step or,
+// in place, k_step_aa) the rotor tiles (first in the list), the actuator line
+// of the next step (k_alm, which waits for them on the device), then the rest,
+// allowed to overlap both; the step counter is advanced by the last launch.
 // diag_step: the step is a diagnostic step (never inside a captured graph).
 lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
 {
@@ -437,6 +451,8 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
     if (b->staged) {
         CK(launch_step(b->coll, b->store, dim3(std::min(b->n_tiles, b->staged_grid)), block, b->stream, a, false,
                        false));
+        if (b->n_rotor > 0)  // the actuator line of the next step, after it
+            CK(launch_alm(b->store, alm_args(b, b->d_step, parity, 0, parity ^ 1, 0), b->stream, false));
         return LBM_OK;
     }
     const unsigned R = b->n_rotor, Nf = b->n_face, Np = b->n_tiles - b->n_rotor - b->n_face;
@@ -448,13 +464,17 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
         ar.write_step = Nb == 0 ? 1 : 0;
         ab.tiles = b->d_tiles + R;
         ab.n_tiles = Nb;
-        if (R > 0) CK(launch_step_aa(b->coll, b->store, dim3(R), block, b->stream, ar, parity == 1, true, false));
+        if (R > 0) {
+            CK(launch_step_aa(b->coll, b->store, dim3(R), block, b->stream, ar, parity == 1, true, false));
+            // after an even step the pulled populations of a cell are its own opposite slots
+            CK(launch_alm(b->store, alm_args(b, b->d_step, parity, 0, 0, parity == 1 ? 0 : 1), b->stream, true));
+        }
         if (Nb > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nb), block, b->stream, ab, parity == 1, false, R > 0));
         return LBM_OK;
     }
-    // rotor tiles, then the face tiles (the general kernel), then the plain bulk
-    // (k_bulk); each launch may start while the one before still runs, the last
-    // one advances the step counter
+    // rotor tiles and the actuator line, then the face tiles (the general
+    // kernel), then the plain bulk (k_bulk); each launch may start while the one
+    // before still runs, the last one advances the step counter
     StepArgs ar = a, af = a, ap = a;
     ar.n_tiles = R;
     ar.write_step = (Nf + Np) == 0 ? 1 : 0;
@@ -465,7 +485,10 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
     af.trigger = Np > 0 ? 1 : 0;
     ap.tiles = b->d_tiles + R + Nf;
     ap.n_tiles = Np;
-    if (R > 0) CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));
+    if (R > 0) {
+        CK(launch_step(b->coll, b->store, dim3(R), block, b->stream, ar, true, false));
+        CK(launch_alm(b->store, alm_args(b, b->d_step, parity, 0, parity ^ 1, 0), b->stream, true));
+    }
     if (Nf > 0) CK(launch_step(b->coll, b->store, dim3(Nf), block, b->stream, af, false, R > 0));
     if (Np > 0) {
         BulkParams bp{};
@@ -506,7 +529,7 @@ lbm_status refresh_alm(Batch* b)
     bool any = false;
     for (auto& I : b->inst) any = any || I.h.n_el > 0;
     if (!any) return LBM_OK;
-    CK(launch_alm(b->store, b->d_dom, (int)b->inst.size(), (int)(b->host_step & 1), b->host_step, b->stream));
+    CK(launch_alm(b->store, alm_args(b, nullptr, 0, b->host_step, (int)(b->host_step & 1), 0), b->stream, false));
     return LBM_OK;
 }
 
@@ -1518,10 +1541,11 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
     lbm_status s = sync_descriptors(b);
     if (s != LBM_OK) return s;
     // the same split as launch_one
-    if (b->staged) *launches = 1;
-    else if (b->inplace) *launches = (b->n_rotor > 0 ? 1 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
+    // (with rotors: the rotor tiles and the actuator line)
+    if (b->staged) *launches = 1 + (b->n_rotor > 0 ? 1 : 0);
+    else if (b->inplace) *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
     else
-        *launches = (b->n_rotor > 0 ? 1 : 0) + (b->n_face > 0 ? 1 : 0) +
+        *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_face > 0 ? 1 : 0) +
                     (b->n_tiles > b->n_rotor + b->n_face ? 1 : 0);
     return LBM_OK;
 }

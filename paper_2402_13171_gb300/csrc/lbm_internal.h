@@ -77,13 +77,11 @@ struct DevDomain {
     float4* el_pos[2];         // by step parity: element position (xyz) and 1/(Sx Sy Sz) (w)
     float4* el_force[2];       // by step parity: blade force (xyz)
     double* el_load;           // scratch, 2 doubles per element
-    float4* el_corner;         // scratch, 8 corners x (rho, u) per element
     double* loads[2];          // by step parity: thrust, torque per rotor
     double* loads_sink;        // mapped page-locked host ring, or nullptr: step s's loads at [(s % sink_len) n_turb + t] * 2
     int sink_len;
     int n_el;
-    unsigned int* rotor_counter;
-    int n_rotor_tiles;
+    unsigned int* rotor_counter;  // CTAs of the actuator-line launch done (the last adds up the loads)
     int diag_every;
     double* diag_acc;          // 4 doubles, accumulated on a diagnostic step
     double* diag_res;          // 4 doubles + the step they belong to
@@ -123,9 +121,36 @@ struct BulkParams {
     LatHot lat[kMaxInstances];
 };
 
+// Arguments of the actuator-line launch (k_alm): one CTA per block of
+// kAlmBlock blade elements of each lattice, the last CTA of a lattice adding up
+// its per-rotor FP64 loads.
+constexpr int kAlmBlock = 32;
+struct AlmArgs {
+    const DevDomain* dom;               // device array
+    int n_inst;
+    int cta_off[kMaxInstances + 1];     // first CTA of each lattice; cta_off[n_inst] = grid size
+    const long long* step_slot;         // in a time step: step n in slot [slot], the launch evaluates n + 1;
+    int slot;                           //   nullptr: evaluate `step`
+    long long step;
+    int array;                          // PDF array read, f[array]
+    int swapped;                        // in-place array after an even step: pulled values in the own opposite slots
+};
+// CTA offsets of the lattices for element counts n_el[0..n_inst); returns the grid size.
+inline int alm_blocks(AlmArgs& a, const int* n_el, int n_inst)
+{
+    int c = 0;
+    a.n_inst = n_inst;
+    for (int i = 0; i < n_inst; ++i) {
+        a.cta_off[i] = c;
+        c += (n_el[i] + kAlmBlock - 1) / kAlmBlock;
+    }
+    a.cta_off[n_inst] = c;
+    return c;
+}
+
 // Planes a rotor tile covers at most (consecutive z-blocks of its column are
 // merged up to this depth), so that one CTA culls the blade elements once for
-// several planes and the rotor launch stays within one wave.
+// several planes.
 constexpr int kRotorPlanes = 3;
 
 // Work-list entry: bit 63 rotor tile, bits 56..62 planes - 1 (rotor tiles),
@@ -184,7 +209,10 @@ cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStrea
 // Outlet copies of an in-place lattice for step `step`, from its current state.
 cudaError_t launch_outlet_fill(int store, const DevDomain* d_dom_inst, const DevDomain& h, long long step,
                                cudaStream_t s);
-cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s);
+// The actuator line (k_alm over alm_blocks' grid).  dependent: launched right
+// after its step's rotor launch, which it waits for on the device while the
+// launches after it may already start (programmatic stream serialization).
+cudaError_t launch_alm(int store, const AlmArgs& a, cudaStream_t s, bool dependent);
 int staged_blocks_per_sm(int coll, int store, int width);
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s);
 cudaError_t launch_init(int store, const DevDomain* d_dom_inst, const DevDomain& h, const double* rho,

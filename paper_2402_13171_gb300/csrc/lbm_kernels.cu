@@ -5,11 +5,13 @@
 // (body force + regularised blade forces, Sec. 2.2, gathered in the
 // rotor box), collision (cumulant, Sec. 2.1 / Geier et al. 2015, or BGK with a
 // Smagorinsky eddy viscosity), store.  PDFs live in HBM as offsets h = f - w
-// in the storage type; all arithmetic is FP32.  A step is two launches: the
-// tiles covering the rotor boxes, then the rest, which overlaps the first.  The
-// last rotor tile to finish evaluates the actuator line for the next step
-// (blade kinematics of Algorithm 2, trilinear sampling, blade-element forces,
-// FP64 rotor loads) while the bulk of the lattice streams.
+// in the storage type; all arithmetic is FP32.  A step with rotors is three
+// launches: the tiles covering the rotor boxes (with the gather of the
+// regularised blade forces); the actuator line of the next step (k_alm: blade
+// kinematics of Algorithm 2, trilinear sampling, blade-element forces, FP64
+// rotor loads), which waits on the device for the rotor tiles; and the rest of
+// the lattice, which starts as soon as the rotor and actuator-line CTAs are
+// resident and overlaps both.
 #include "lbm_internal.h"
 
 #include <cuda_bf16.h>
@@ -776,8 +778,8 @@ __device__ __forceinline__ void polar_lookup(const DevTurbine* B, float x, float
     CD = B->cd[lo] + t * (B->cd[lo + 1] - B->cd[lo]);
 }
 
-// Sum of the ALM force boxes containing cell (x, y, z) (written by this or the
-// previous launch; read through L2).
+// Sum of the ALM force boxes containing cell (x, y, z): the force of the last
+// collision (read through L2).
 __device__ __forceinline__ void alm_box_force(const DevDomain* D, int x, int y, int z, float F[3])
 {
     for (int t = 0; t < D->n_turb; ++t) {
@@ -854,35 +856,39 @@ __device__ __forceinline__ float tip_loss_factor(int n_blades, float R, float r,
     return 0.63661977f * acosf(expf(-f));  // 2/pi
 }
 
-// Actuator line of step `step` for one lattice, by the whole CTA.  Reads the
-// populations of the current array f (post-collision of step-1) and the box
-// force of step-1; writes element positions with their spreading
-// normalisation, blade forces, and per-rotor FP64 thrust and torque into the
-// buffers of parity step & 1.
+// Actuator line of step `step` for the blade elements [e0, e0 + kAlmBlock) of
+// one lattice, by the whole CTA.  Reads the populations of the current array f
+// (post-collision of step-1) and the box force of step-1; writes the element
+// positions with their spreading normalisation, blade forces and FP64 load
+// parts of those elements into the buffers of parity step & 1.
+//  phase 0, one thread per element: blade kinematics (Algorithm 2);
 //  phase 1, one thread per (element, corner): pull the 27 populations of the
 //    corner cell, rho and u = (sum c f + F/2)/rho at the corner;
 //  phase 2, one thread per element: trilinear blend, relative velocity,
 //    angle of attack, polars, blade force (with the tip-loss factor if set),
-//    kernel normalisation, FP64 loads;
-//  phase 3, warp 0: per-rotor FP64 sums in a fixed order (also written to the
-//    host loads sink when one is set).
+//    kernel normalisation, FP64 load parts.
+// Each element's values depend on that element alone, so blocks of elements
+// may run in separate CTAs.
 template <typename T>
-__device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long long step, int swapped = 0)
+__device__ __noinline__ void alm_block(const DevDomain* D, const T* f, long long step, int swapped, int e0)
 {
+    __shared__ ElementGeo s_geo[kAlmBlock];
+    __shared__ float4 s_corner[8 * kAlmBlock];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
     const int par = (int)(step & 1);
     const long long N = D->N;
     const int n[3] = {D->nx, D->ny, D->nz};
-    for (int pc = tid; pc < 8 * D->n_el; pc += nthr) {
-        const int g = pc >> 3, cn = pc & 7;
-        ElementGeo G;
-        element_geometry(D, g, step, G);
+    const int ne = min(kAlmBlock, D->n_el - e0);
+    for (int i = tid; i < ne; i += nthr) element_geometry(D, e0 + i, step, s_geo[i]);
+    __syncthreads();
+    for (int pc = tid; pc < 8 * ne; pc += nthr) {
+        const int i = pc >> 3, cn = pc & 7;
         int c[3];
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int i0 = (int)floorf(G.p[a]);
+            const int i0 = (int)floorf(s_geo[i].p[a]);
             if (i0 < 1 || i0 + 1 > n[a] - 2) inside = false;
             c[a] = i0 + ((cn >> a) & 1);
         }
@@ -915,12 +921,12 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
         } else if (cn == 0) {
             atomicOr(D->err, ERR_ELEMENT_OUTSIDE);
         }
-        D->el_corner[pc] = out;
+        s_corner[pc] = out;
     }
     __syncthreads();
-    for (int g = tid; g < D->n_el; g += nthr) {
-        ElementGeo G;
-        element_geometry(D, g, step, G);
+    for (int i = tid; i < ne; i += nthr) {
+        const int g = e0 + i;
+        const ElementGeo G = s_geo[i];
         const DevTurbine* B = G.B;
         float fr[3];
 #pragma unroll
@@ -930,7 +936,7 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
         for (int cn = 0; cn < 8; ++cn) {
             const float w = ((cn & 1) ? fr[0] : 1.0f - fr[0]) * (((cn >> 1) & 1) ? fr[1] : 1.0f - fr[1]) *
                             (((cn >> 2) & 1) ? fr[2] : 1.0f - fr[2]);
-            const float4 q = D->el_corner[8 * g + cn];
+            const float4 q = s_corner[8 * i + cn];
             rho_p += w * q.x;
             u_p[0] += w * q.y;
             u_p[1] += w * q.z;
@@ -970,10 +976,10 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
             const int lo = (int)ceilf(G.p[a] - B->cut), hi = (int)floorf(G.p[a] + B->cut);
             float sa = 0.0f;
             if (B->roma) {
-                for (int i = lo; i <= hi; ++i) sa += roma_phi((float)i - G.p[a]);
+                for (int j = lo; j <= hi; ++j) sa += roma_phi((float)j - G.p[a]);
             } else {
-                for (int i = lo; i <= hi; ++i) {
-                    const float d = (float)i - G.p[a];
+                for (int j = lo; j <= hi; ++j) {
+                    const float d = (float)j - G.p[a];
                     sa += expf(-d * d * B->inv_eps2);
                 }
             }
@@ -986,14 +992,23 @@ __device__ __noinline__ void alm_compute(const DevDomain* D, const T* f, long lo
             (double)G.r * ((double)Fb[0] * G.et[0] + (double)Fb[1] * G.et[1] + (double)Fb[2] * G.et[2]);
     }
     __syncthreads();
+}
+
+// Per-rotor FP64 thrust and torque of step `step` from the elements' load
+// parts, by warp 0 of the CTA in a fixed order (lane-strided partial sums, then
+// a butterfly), also written to the host loads sink when one is set.
+__device__ __forceinline__ void alm_loads(const DevDomain* D, long long step)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int par = (int)(step & 1);
     if (tid < 32) {
         for (int t = 0; t < D->n_turb; ++t) {
             const DevTurbine* B = D->turb + t;
             const int ne = B->n_blades * B->n_elements;
             double th = 0.0, tq = 0.0;
             for (int e = tid; e < ne; e += 32) {
-                th += D->el_load[2 * (B->el_offset + e)];
-                tq += D->el_load[2 * (B->el_offset + e) + 1];
+                th += __ldcg(D->el_load + 2 * (B->el_offset + e));
+                tq += __ldcg(D->el_load + 2 * (B->el_offset + e) + 1);
             }
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
@@ -1197,17 +1212,14 @@ __device__ __forceinline__ int cull_rotor_elements(const DevDomain* D, unsigned 
 // The update of one rotor tile: cull the blade elements whose support reaches
 // the tile into shared memory (in element order; when more than KCULL reach it
 // every cell scans all elements), then each cell as in the bulk path plus the
-// regularised blade force (Gaussian or Roma), and in the last rotor tile of its
-// lattice to finish, the actuator line of the next step.  CTA-wide; only the rotor
-// launch of k_step contains it.  Writes the thread's diagnostic partial sums
-// (zero unless diag) to sums[4].
+// regularised blade force (Gaussian or Roma).  CTA-wide; only the rotor launch
+// of k_step contains it.  Writes the thread's diagnostic partial sums (zero
+// unless diag) to sums[4].
 template <int COLL, typename T, bool MARCH, int KCULL>
 __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned long long tile, long long step, int parity,
                                                int planes, bool diag, float4* s_pos, float4* s_frc, int* s_tag,
-                                               int* s_cnt, int* s_flag, double* sums)
+                                               int* s_cnt, double* sums)
 {
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthreads = blockDim.x * blockDim.y;
     const int z0 = (int)((tile >> 32) & 0xFFFF);
     const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
     const int x = (int)(tile & 0xFFFF) + threadIdx.x;
@@ -1255,20 +1267,6 @@ __device__ __forceinline__ void rotor_tile_update(const DevDomain* D, unsigned l
     sums[1] = (double)o_jx;
     sums[2] = (double)o_jy;
     sums[3] = (double)o_jz;
-
-    // last rotor tile of this lattice: actuator line of the next step
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(D->rotor_counter, 1u);
-        *s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
-    }
-    __syncthreads();
-    if (*s_flag) {
-        __threadfence();
-        alm_compute<T>(D, dst, step + 1);
-        if (tid == 0) *D->rotor_counter = 0u;
-    }
 }
 
 // One time step over the work list, as two launches of this kernel: ROTOR over
@@ -1321,11 +1319,11 @@ __device__ __forceinline__ void diag_close(const StepArgs& A, const DevDomain* D
     }
 }
 
-// The rotor CTAs allow the dependent (bulk) launch to start as soon as they are
-// all running, so the two overlap and the actuator line of the next step,
-// evaluated by the last rotor CTA, runs under the bulk.  The two launches
-// write disjoint cells.  The bulk launch's last CTA waits for the rotor launch
-// before it exits, so the bulk launch ends only after both.
+// The rotor CTAs allow the dependent launch (the actuator line, whose CTAs do
+// the same for the bulk) to start as soon as they are all running, so the
+// bulk overlaps the rotor tiles and the actuator line of the next step.  The
+// launches write disjoint cells.  Each launch's last CTA waits for the launch
+// before it before it exits, so the bulk launch ends only after all of them.
 // Register budgets (blocks of up to 256 threads): 64 per thread for the
 // single-plane cumulant bulk, whose collision fits them without spills, so 8
 // CTAs of 128 threads (32 warps) are resident per SM; 85 for the rotor tiles
@@ -1336,9 +1334,8 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
     if (ROTOR || A.trigger) asm volatile("griddepcontrol.launch_dependents;");
     constexpr int kCull = 128;  // blade elements kept per rotor tile
     __shared__ double s_red[8][4];
-    __shared__ int s_flag;
-    __shared__ float4 s_pos[kCull], s_frc[kCull];
-    __shared__ int s_tag[kCull];
+    __shared__ float4 s_pos[ROTOR ? kCull : 1], s_frc[ROTOR ? kCull : 1];
+    __shared__ int s_tag[ROTOR ? kCull : 1];
     __shared__ int s_cnt[8];
     const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
     const int inst = tile_lattice(tile);
@@ -1356,13 +1353,11 @@ __global__ void __launch_bounds__(256, MARCH ? 2 : ((ROTOR || COLL != COLL_CUMUL
     // in FP64 when it marches over several planes
     using Acc = typename std::conditional<MARCH, double, float>::type;
     Acc o_m = 0, o_jx = 0, o_jy = 0, o_jz = 0;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthreads = blockDim.x * blockDim.y;
 
     if constexpr (ROTOR) {
         double sums[4];
         rotor_tile_update<COLL, T, MARCH, kCull>(D, tile, step, A.parity, tile_planes(tile), diag, s_pos, s_frc,
-                                                 s_tag, s_cnt, &s_flag, sums);
+                                                 s_tag, s_cnt, sums);
         o_m = sums[0];
         o_jx = sums[1];
         o_jy = sums[2];
@@ -1860,11 +1855,11 @@ __device__ __forceinline__ void aa_cell(const DevDomain* D, int x, int y, int z,
     }
 }
 
-// The time step on a single PDF array (the AA pattern), as two launches like
-// k_step: ROTOR over the rotor tiles (element culling, force gather, and in
-// the last rotor tile of a lattice the actuator line of the next step, whose
-// sampling reads the array in the layout this step leaves), then the rest,
-// which may overlap it.  Rotor tiles cover up to kRotorPlanes planes, one
+// The time step on a single PDF array (the AA pattern), as launches like
+// k_step: ROTOR over the rotor tiles (element culling, force gather; the
+// actuator line of the next step follows as its own launch, whose sampling
+// reads the array in the layout this step leaves), then the rest, which may
+// overlap them.  Rotor tiles cover up to kRotorPlanes planes, one
 // after the other; bulk tiles one plane.
 template <int COLL, typename T, bool ODD, bool ROTOR>
 __global__ void __launch_bounds__(256, ROTOR ? 2 : (COLL == COLL_CUMULANT ? 4 : 3)) k_step_aa(const StepArgs A)
@@ -1872,7 +1867,6 @@ __global__ void __launch_bounds__(256, ROTOR ? 2 : (COLL == COLL_CUMULANT ? 4 : 
     if (ROTOR) asm volatile("griddepcontrol.launch_dependents;");
     constexpr int kCull = 128;
     __shared__ double s_red[8][4];
-    __shared__ int s_flag;
     __shared__ float4 s_pos[ROTOR ? kCull : 1], s_frc[ROTOR ? kCull : 1];
     __shared__ int s_tag[ROTOR ? kCull : 1];
     __shared__ int s_cnt[8];
@@ -1905,22 +1899,6 @@ __global__ void __launch_bounds__(256, ROTOR ? 2 : (COLL == COLL_CUMULANT ? 4 : 
                     o_jz += jz;
                 }
             }
-        }
-        // last rotor tile of this lattice: actuator line of the next step, from
-        // the array in the layout this step leaves (after an even step the
-        // pulled populations of cell x are its own opposite slots)
-        __syncthreads();
-        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        if (tid == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(D->rotor_counter, 1u);
-            s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_flag) {
-            __threadfence();
-            alm_compute<T>(D, (const T*)D->f[0], step + 1, ODD ? 0 : 1);
-            if (tid == 0) *D->rotor_counter = 0u;
         }
     } else {
         if (x < D->nx && y < D->ny) {
@@ -2059,7 +2037,7 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
     extern __shared__ __align__(128) unsigned char stage_raw[];
     __shared__ __align__(8) unsigned long long s_full[kMaxStages];
     __shared__ double s_red[8][4];
-    __shared__ int s_flag, s_abort;
+    __shared__ int s_abort;
     __shared__ float4 s_pos[kCull], s_frc[kCull];
     __shared__ int s_tag[kCull];
     __shared__ int s_cnt[8];
@@ -2261,21 +2239,6 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
                     atomicAdd(D->diag_acc + kk, sum);
                 }
         }
-        // last rotor segment of this lattice: actuator line of the next step
-        if (rotor_tile) {
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                const unsigned prev = atomicAdd(D->rotor_counter, 1u);
-                s_flag = (prev == (unsigned)D->n_rotor_tiles - 1u) ? 1 : 0;
-            }
-            __syncthreads();
-            if (s_flag) {
-                __threadfence();
-                alm_compute<T>(D, dst, step + 1);
-                if (tid == 0) *D->rotor_counter = 0u;
-            }
-        }
     }
     // after a failed wait: the copies still in flight (segments k .. issued - 1)
     // land before the CTA exits, each wait bounded again, by the full limit
@@ -2309,11 +2272,36 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
     }
 }
 
+// The actuator line as its own launch: CTA b of a lattice evaluates its
+// elements [32 b, 32 b + 32), and the last of the lattice's CTAs to finish adds
+// up the per-rotor loads.  In a time step it follows the rotor launch: it lets
+// the step's next launch start at once, then waits on the device until the
+// rotor tiles (which write the cells it samples and the box force) are done.
 template <typename T>
-__global__ void k_alm(const DevDomain* dom, int parity, long long step)
+__global__ void __launch_bounds__(256) k_alm(const AlmArgs A)
 {
-    const DevDomain* D = dom + blockIdx.x;
-    if (D->n_el > 0) alm_compute<T>(D, (const T*)D->f[parity], step);
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    __shared__ int s_last;
+    int inst = 0;
+    while (inst + 1 < A.n_inst && A.cta_off[inst + 1] <= (int)blockIdx.x) ++inst;
+    const DevDomain* D = A.dom + inst;
+    const int lb = (int)blockIdx.x - A.cta_off[inst];
+    const int nb = A.cta_off[inst + 1] - A.cta_off[inst];
+    const long long step = A.step_slot ? __ldcg(A.step_slot + A.slot) + 1 : A.step;
+    alm_block<T>(D, (const T*)D->f[A.array], step, A.swapped, lb * kAlmBlock);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(D->rotor_counter, 1u);
+        s_last = prev == (unsigned)nb - 1u ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        alm_loads(D, step);
+        if (tid == 0) *D->rotor_counter = 0u;
+    }
 }
 
 // Inlet ghost populations of every column for step `step` (after a state change).
@@ -2584,12 +2572,26 @@ int staged_blocks_per_sm(int coll, int store, int width)
     return n;
 }
 
-cudaError_t launch_alm(int store, const DevDomain* d_dom, int n_inst, int parity, long long step, cudaStream_t s)
+cudaError_t launch_alm(int store, const AlmArgs& a, cudaStream_t s, bool dependent)
 {
-    if (store == STORE_FP32) k_alm<float><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
-    else if (store == STORE_BF16) k_alm<__nv_bfloat16><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
-    else k_alm<__half><<<n_inst, 256, 0, s>>>(d_dom, parity, step);
-    return cudaGetLastError();
+    const int grid = a.cta_off[a.n_inst];
+    if (grid == 0) return cudaSuccess;
+    void (*k)(AlmArgs) = store == STORE_FP32 ? k_alm<float> : (store == STORE_BF16 ? k_alm<__nv_bfloat16> : k_alm<__half>);
+    if (!dependent) {
+        k<<<grid, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 cudaError_t launch_inflow(const DevDomain* d_dom_inst, const DevDomain& h, long long step, cudaStream_t s)

@@ -44,7 +44,6 @@ struct StaticScratch {
     DevTurbine turb;
     float4 el_pos[2][kStaticMaxElements];
     float4 el_force[2][kStaticMaxElements];
-    float4 el_corner[8 * kStaticMaxElements];
     double el_load[2 * kStaticMaxElements];
     double loads[2][2];
     float table[3 * kStaticMaxPolar + kStaticMaxElements];  // alpha, cl, cd, twist
@@ -53,6 +52,19 @@ struct StaticScratch {
 };
 
 static __device__ __align__(256) StaticScratch g_alm_static;
+
+// The actuator-line launch over the block's one lattice, of step `step`.
+static AlmArgs alm_args_static(const DevDomain* d_dom, int n_el, long long step)
+{
+    AlmArgs a{};
+    a.dom = d_dom;
+    alm_blocks(a, &n_el, 1);
+    a.step_slot = nullptr;
+    a.step = step;
+    a.array = 0;
+    a.swapped = 0;
+    return a;
+}
 
 namespace {
 std::mutex g_mu;
@@ -186,7 +198,6 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
         D.loads[p] = d_loads + 2 * p;
     }
     D.el_load = member<double>(S, offsetof(StaticScratch, el_load));
-    D.el_corner = member<float4>(S, offsetof(StaticScratch, el_corner));
     D.n_el = n_el;
     D.rotor_counter = member<unsigned int>(S, offsetof(StaticScratch, rotor_counter));
     D.err = d_err;
@@ -204,7 +215,7 @@ extern "C" lbm_status alm_eval_static(const float* pdf_offsets, int nx, int ny, 
         cudaMemcpyAsync(d_turb, &B, sizeof B, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_dom, &D, sizeof D, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(d_err, 0, sizeof(unsigned int), st) != cudaSuccess ||
-        launch_alm(STORE_FP32, d_dom, 1, 0, step, st) != cudaSuccess ||
+        launch_alm(STORE_FP32, alm_args_static(d_dom, n_el, step), st, false) != cudaSuccess ||
         cudaMemcpy2DAsync(elem_force, 3 * sizeof(float), d_force + (size_t)par * kStaticMaxElements, sizeof(float4),
                           3 * sizeof(float), n_el, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(loads, d_loads + 2 * par, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)

@@ -167,7 +167,7 @@ def test_inplace_rotor_inlet_outlet_equals_two_arrays_bitwise(collision, storage
     dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777, kernel=kernel)
     dom["collision"] = collision
     g2, ga = _rotor_pair(dom, [turb], storage, diag_every=4)
-    assert ga.launches_per_step() == 2
+    assert ga.launches_per_step() == 3  # rotor tiles, actuator line, the rest
     _same_run(g2, ga, 1)
     d2, s2 = g2.diagnostics()
     da, sa = ga.diagnostics()

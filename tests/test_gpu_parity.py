@@ -295,6 +295,36 @@ def test_staged_batch_matches_direct():
         np.testing.assert_allclose(da, db, rtol=0, atol=1e-9)
 
 
+def test_two_rotors_of_many_elements():
+    """Two rotors of 3 x 40 elements on one lattice, one of them yawed: the
+    actuator-line launch runs 8 CTAs of 32 elements (the second rotor starting
+    inside the fourth), the last adding up the loads.  Flow, element positions
+    and forces and both rotors' loads follow the oracle, and the staged kernel
+    (its own element culling per row segment) steps bit for bit like the direct
+    one."""
+    nx = 112
+    dom, t1 = I.single_turbine_case(nx, 40, 40, diameter=16.0, elements_per_blade=40, seed=93, hub=(28.0, 20.0, 20.0))
+    t2 = I.single_turbine(nx, 40, 40, diameter=16.0, elements_per_blade=40, hub=(72.0, 20.5, 19.5), yaw=0.12,
+                          tsr=5.0)
+    rho, u, fneq = I.random_state(nx, 40, 40, seed=9, u_mean=(0.04, 0.0, 0.0), du=0.01)
+    ga, s = setup_pair(dom, [t1, t2], rho=rho, u=u, fneq=fneq, inflow=True, diag_every=3)
+    gb, _ = setup_pair(dom, [t1, t2], rho=rho, u=u, fneq=fneq, inflow=True, diag_every=3, tile=(64, 1, 1, 1))
+    assert ga.launches_per_step() == 3 and gb.launches_per_step() == 2
+    ga.step(7)
+    gb.step(7)
+    s.step(7)
+    _rotor_checks(ga, s, [t1, t2], "two rotors")
+    np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
+    for t in (0, 1):
+        tha, tqa, efa, epa = ga.loads(t, elements=True)
+        thb, tqb, efb, epb = gb.loads(t, elements=True)
+        assert (tha, tqa) == (thb, tqb)
+        np.testing.assert_array_equal(efa, efb)
+        np.testing.assert_array_equal(epa, epb)
+    ga.destroy()
+    gb.destroy()
+
+
 def test_autotune_keeps_state_and_results(tmp_path):
     """The tuner times tile candidates on the live state and restores it: the
     run continues exactly as an untuned one."""
@@ -330,8 +360,9 @@ def test_graph_replay_equals_direct_launches():
     np.testing.assert_array_equal(ga.pdfs(), gb.pdfs())
     ms, n = gb.kernel_time()
     assert n == 9 and ms > 0
-    # a step is the rotor-tile launch plus the rest; without a rotor, one launch
-    assert gb.launches_per_step() == 2
+    # a step is the rotor-tile launch, the actuator line and the rest; without a
+    # rotor, one launch
+    assert gb.launches_per_step() == 3
     g0 = gpu_lattice(dom)
     assert g0.launches_per_step() == 1
     g0.destroy()
