@@ -96,45 +96,25 @@ def job_mlups(world, cells, steps, elapsed_ms):
 
 
 # DRAM bytes per time step (dram__bytes_read.sum + dram__bytes_write.sum over
-# the step's k_step launches: the rotor tiles and the rest) of the single-rotor
-# workload at every tile candidate, from one ncu pass over
-# `bench.py --workload tilesweep --steps 1 --warmup 1 --storage <fp32|bf16>`
-# (the second, warm step of each tile), keyed by (workload, storage, collision,
-# tile).  They hold for the kernel source whose comment-free SHA-256 is
-# recorded and are reported as null once the code changes.
+# the step's three launches: the rotor tiles, the actuator line and the rest)
+# of the single-rotor workload at the tiles the tuner picks from, each from one
+# ncu capture of one step of
+# `bench.py --steps 8 --warmup 4 --storage <fp32|bf16> --tile <tile> --no-e2e
+# --no-cpu-baseline --no-bf16` (-k regex:"k_step|k_bulk|k_alm" -s 10 -c 3), keyed
+# by (workload, storage, collision, tile).  They hold for the kernel source
+# whose comment-free SHA-256 is recorded and are reported as null once the code
+# changes.
 NCU_TRAFFIC = {
-    "kernel_sha256": "75b75f4c270f56a1af4ea211360b355ac31c325f0a17dd5839428252a63c39c8",
+    "kernel_sha256": "bd420f5940d316845b98868172565fcdbbe990764fb572855bf9039bded9c7b0",
     "bytes": {
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x1"): 464112640 + 387036928,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x1"): 464276736 + 386765312,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x8x1"): 463891968 + 389096704,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x1"): 458871552 + 371892480,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1"): 459077632 + 374371840,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1"): 458771712 + 371240192,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x2"): 464128512 + 387454464,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x4"): 464071424 + 386048000,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x4"): 464133376 + 386793984,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x8"): 464292608 + 389327360,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x4"): 458810624 + 371303424,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x8"): 464311296 + 387358208,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1 staged"): 585385216 + 410043136,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1 staged"): 478589952 + 400725760,
-        ("single_turbine_256x128x128", "fp32", "cumulant", "256x1x1 staged"): 454932224 + 401753856,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x1"): 242803712 + 176186368,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x1"): 243053056 + 177562368,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x8x1"): 242721280 + 180068096,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x1"): 234975488 + 166383872,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1"): 235050496 + 168000512,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1"): 234799872 + 166830080,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x2"): 243043840 + 177526528,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x4"): 242934016 + 176663552,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x4"): 242990080 + 175754240,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x8"): 243048448 + 178149120,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x4"): 234954496 + 166675712,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x8"): 242880512 + 175757312,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1 staged"): 255268864 + 183737600,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1 staged"): 243163392 + 181556736,
-        ("single_turbine_256x128x128", "bf16", "cumulant", "256x1x1 staged"): 227442944 + 181490944,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x4x1"): 464984832 + 385754112,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x8x1"): 464846592 + 385864192,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1"): 460055040 + 370142464,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x1"): 459879680 + 369477632,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x1"): 243681536 + 176297728,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x8x1"): 243550208 + 176582400,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1"): 236118272 + 164203520,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x1"): 236024576 + 163678464,
     },
 }
 
@@ -512,9 +492,11 @@ def run_ours(args):
         k16, _ = lb.kernel_time()
         ms16, k16 = reduce_max([ms16, k16], dist, device="cuda")
         ach16 = achieved_gbs(bpc16, cells, k16 * 1e-3)
+        tile16 = tile_label(lb.tile())
         bf16 = {"value": job_mlups(world, cells, args.steps, ms16), "unit": "MLUPS", "ms_per_step": ms16 / args.steps,
-                "tile": "x".join(map(str, lb.tile()[:3])),
+                "tile": tile16,
                 "roofline": {"bound": "hbm", "achieved": ach16, "peak": peak, "unit": "GB/s", "frac": ach16 / peak,
+                             "traffic": measured_traffic(workload, "bf16", args.collision, tile16),
                              "bytes_per_cell": bpc16, "kernel_ms": k16}}
         lb.destroy()
 
@@ -550,7 +532,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": measured_traffic(workload, args.storage, args.collision, tile_used),
-                         "kernel": "k_step (fused stream-collide + in-kernel ALM)",
+                         "kernel": "one time step: rotor tiles (k_step), actuator line (k_alm), fused "
+                                   "stream-collide of the rest (k_bulk, k_bulk2 with 16-bit storage)",
                          "bytes_per_cell": bytes_per_cell, "kernel_ms": kernel_ms, "peak_kind": peak_kind},
             "e2e": e2e,
             "gpu_launches": args.steps * launches_per_step,
