@@ -89,8 +89,8 @@ typedef struct {
     int tile_x, tile_y;      /* CTA tile (threads along x, rows along y); 0 = default 32 x 4;
                                 tile_x a multiple of 32, tile_x * tile_y <= 256 */
     int tile_z;              /* planes per CTA, each thread marching through them; 0 = default 1; <= 64 */
-    int staged;              /* kernel form of the step.  0 = direct loads; with 16-bit storage, the
-                                cumulant collision, single-plane tiles and every nx of the batch even,
+    int staged;              /* kernel form of the step.  0 = direct loads; with 16-bit storage,
+                                single-plane tiles and every nx of the batch even,
                                 the tiles without a no-slip or free-slip face cell then take two cells
                                 of a row per thread (32-bit words, the collision on f32x2 instructions
                                 across the pair; bit for bit the one-cell results).

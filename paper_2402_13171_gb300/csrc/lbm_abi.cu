@@ -56,7 +56,7 @@ struct Batch {
     int staged = 0;        // rows staged in shared memory by persistent CTAs
     unsigned staged_grid = 0;
     int single_cell = 0;   // the bulk launch keeps one cell per thread where pairs would apply
-    bool pairs_ok = false; // cumulant collision, 16-bit storage and every nx even: paired bulk cells
+    bool pairs_ok = false; // 16-bit storage and every nx even: paired bulk cells
     lbm_status status = LBM_OK;
     std::string err;
     bool dirty = true;
@@ -595,7 +595,7 @@ lbm_status create_batch(int n, const lbm_config* cfgs, lbm_ctx** out)
     b->inplace = cfgs[0].inplace;
     const int want_staged = cfgs[0].staged;
     b->single_cell = want_staged == 2 ? 1 : 0;
-    b->pairs_ok = b->coll == COLL_CUMULANT && b->store != STORE_FP32;
+    b->pairs_ok = b->store != STORE_FP32;
     for (int i = 0; i < n; ++i)
         if (cfgs[i].nx % 2 != 0) b->pairs_ok = false;
     b->diag_every = cfgs[0].diag_every;

@@ -197,8 +197,8 @@ inline bool turbine_values_finite(const alm_turbine_desc* d)
 // without a wall-face cell (nullptr: the general kernel); diag_step: the step is a
 // diagnostic step (the bulk kernel then carries the FP64 sums; the general
 // kernels read the step's diagnostic flag on the device); pairs: the bulk kernel
-// takes two cells of a row per thread (cumulant collision, 16-bit storage, every
-// nx even), its block (block.x / 2, block.y) over the same tiles.
+// takes two cells of a row per thread (16-bit storage, every nx even), its block
+// (block.x / 2, block.y) over the same tiles.
 cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool rotor,
                         bool dependent, const BulkParams* bulk = nullptr, bool diag_step = false, bool pairs = false);
 // The in-place (AA) step over the whole work list: odd steps read and write a

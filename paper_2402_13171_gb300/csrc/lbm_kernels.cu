@@ -632,53 +632,106 @@ __device__ __forceinline__ void collide_cumulant(float h[27], float Fx, float Fy
 // BGK toward the polynomial equilibrium with a Smagorinsky eddy viscosity
 // (tau = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C^2 |Pi|/rho))/2, Pi the
 // force-corrected non-equilibrium momentum flux) and the Guo source
-// (1 - omega/2) w [3(c - u) + 9 (c.u) c].F.
-__device__ __forceinline__ void collide_srt_smag(float h[27], float Fx, float Fy, float Fz, float tau0, float smag_c2,
-                                                 float& drho_o, float& jx_o, float& jy_o, float& jz_o)
+// (1 - omega/2) w [3(c - u) + 9 (c.u) c].F, on a lane type like the cumulant
+// collision.  The raw moments take the f32x2 pairs of the cumulant collision;
+// everything after them runs, on a pair of cells, as the one-cell scalar
+// instructions lane by lane (sadd, smul, ... below), so the two forms agree bit
+// for bit by construction (the f32x2 form of this part did not, in a fraction of
+// the cells, although each f32x2 instruction rounds as its scalar one).
+__device__ __forceinline__ float sadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ssub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float smul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float sfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float sneg(float a) { return -a; }
+__device__ __forceinline__ float2 sadd(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 ssub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 smul(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 sfma(float2 a, float2 b, float2 c)
 {
-    const Moments M = raw_moments(h);
-    const float rho = 1.0f + M.drho;
-    const float inv = 1.0f / rho;
-    const float ux = (M.jx + 0.5f * Fx) * inv;
-    const float uy = (M.jy + 0.5f * Fy) * inv;
-    const float uz = (M.jz + 0.5f * Fz) * inv;
-    const float third = 1.0f / 3.0f;
-    const float axx = M.Sxx - M.drho * third - rho * ux * ux + ux * Fx;
-    const float ayy = M.Syy - M.drho * third - rho * uy * uy + uy * Fy;
-    const float azz = M.Szz - M.drho * third - rho * uz * uz + uz * Fz;
-    const float axy = M.Sxy - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
-    const float axz = M.Sxz - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
-    const float ayz = M.Syz - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
-    const float P2 = axx * axx + ayy * ayy + azz * azz + 2.0f * (axy * axy + axz * axz + ayz * ayz);
-    const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + 18.0f * 1.41421356237f * smag_c2 * sqrtf(P2) * inv));
-    const float om = 1.0f / tau;
-    const float src = 1.0f - 0.5f * om;
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 sneg(float2 a) { return make_float2(-a.x, -a.y); }
+template <class V>
+__device__ __forceinline__ V vsqrt(V a);
+template <> __device__ __forceinline__ float vsqrt<float>(float a) { return __fsqrt_rn(a); }
+template <> __device__ __forceinline__ float2 vsqrt<float2>(float2 a) { return make_float2(__fsqrt_rn(a.x), __fsqrt_rn(a.y)); }
+
+template <class V>
+__device__ __forceinline__ void collide_srt_smag_v(V h[27], V Fx, V Fy, V Fz, float tau0, float smag_c2, V& drho_o,
+                                                   V& jx_o, V& jy_o, V& jz_o)
+{
+    using P = typename ZPair<V>::T;
+    P hp[9];
+    V hs[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        hp[r] = zmk(h[r], h[18 + r]);
+        hs[r] = h[9 + r];
+    }
+    const MomentsV<V> M = raw_moments_paired<V>(hp, hs);
+    const V rho = sadd(vc<V>(1.0f), M.drho);
+    const V inv = vrcp(rho);
+    const V half = vc<V>(0.5f);
+    const V ux = smul(sfma(half, Fx, M.jx), inv);
+    const V uy = smul(sfma(half, Fy, M.jy), inv);
+    const V uz = smul(sfma(half, Fz, M.jz), inv);
+    const V nux = sneg(ux), nuy = sneg(uy), nuz = sneg(uz);
+    const V rux = smul(rho, ux), ruy = smul(rho, uy);
+    const V mt = vc<V>(-1.0f / 3.0f);
+    // non-equilibrium second moments: S_ab - rho/3 delta - rho u_a u_b + (u_a F_b + u_b F_a)/2
+    const V axx = sfma(ux, Fx, sfma(rux, nux, sfma(M.drho, mt, M.Sxx)));
+    const V ayy = sfma(uy, Fy, sfma(ruy, nuy, sfma(M.drho, mt, M.Syy)));
+    const V azz = sfma(uz, Fz, sfma(smul(rho, uz), nuz, sfma(M.drho, mt, M.Szz)));
+    const V axy = sfma(half, sfma(ux, Fy, smul(uy, Fx)), sfma(rux, nuy, M.Sxy));
+    const V axz = sfma(half, sfma(ux, Fz, smul(uz, Fx)), sfma(rux, nuz, M.Sxz));
+    const V ayz = sfma(half, sfma(uy, Fz, smul(uz, Fy)), sfma(ruy, nuz, M.Syz));
+    const V off = sfma(axy, axy, sfma(axz, axz, smul(ayz, ayz)));
+    const V P2 = sfma(axx, axx, sfma(ayy, ayy, sfma(azz, azz, sadd(off, off))));
+    const V arg = sfma(smul(vc<V>(18.0f * 1.41421356237f * smag_c2), vsqrt(P2)), inv, vc<V>(tau0 * tau0));
+    const V tau = smul(half, sadd(vc<V>(tau0), vsqrt(arg)));
+    const V om = vrcp(tau);
+    const V src = sfma(om, vc<V>(-0.5f), vc<V>(1.0f));
+    const V uu = sfma(ux, ux, sfma(uy, uy, smul(uz, uz)));
+    const V uF = sfma(ux, Fx, sfma(uy, Fy, smul(uz, Fz)));
     // h* = (1 - om) h + om feq + S, evaluated for each pair q, qbar = 26 - q
     // together: c.u and c.F change sign with c, so om feq + S splits into a part
     // even in c, w (om (drho + rho (4.5 (c.u)^2 - 1.5 u^2)) + src (9 (c.u)(c.F) - 3 u.F)),
-    // and an odd part, w 3 (om rho c.u + src c.F)
-    const float a = 1.0f - om;
-    const float om_rho = om * rho;
-    const float k1 = 4.5f * om_rho;
-    const float s9 = 9.0f * src;
-    const float k0 = fmaf(-1.5f * om_rho, uu, fmaf(om, M.drho, -3.0f * src * uF));
+    // and an odd part, w 3 (om rho c.u + src c.F); c.u and c.F are formed for
+    // the member of the pair whose first nonzero component (z, then y, then x)
+    // is +1, so the sums start without a sign change
+    const V a = ssub(vc<V>(1.0f), om);
+    const V om_rho = smul(om, rho);
+    const V k1 = smul(vc<V>(4.5f), om_rho);
+    const V s9 = smul(vc<V>(9.0f), src);
+    const V k0 = sfma(smul(vc<V>(-1.5f), om_rho), uu, sfma(om, M.drho, smul(smul(vc<V>(-3.0f), src), uF)));
+    auto dot = [](int cx, int cy, int cz, V x, V y, V z) {
+        V r = cz != 0 ? z : (cy != 0 ? y : x);  // the first nonzero component, +1
+        if (cz != 0 && cy != 0) r = cy > 0 ? sadd(r, y) : ssub(r, y);
+        if ((cz != 0 || cy != 0) && cx != 0) r = cx > 0 ? sadd(r, x) : ssub(r, x);
+        return r;
+    };
 #pragma unroll
-    for (int q = 0; q < 13; ++q) {
-        const float cx = (float)qcx(q), cy = (float)qcy(q), cz = (float)qcz(q);
-        const float cu = cx * ux + cy * uy + cz * uz;
-        const float cF = cx * Fx + cy * Fy + cz * Fz;
-        const float pe = wq(q) * fmaf(cu, fmaf(k1, cu, s9 * cF), k0);
-        const float po = (3.0f * wq(q)) * fmaf(om_rho, cu, src * cF);
-        h[q] = fmaf(a, h[q], pe + po);
-        h[26 - q] = fmaf(a, h[26 - q], pe - po);
+    for (int p = 0; p < 13; ++p) {
+        const int q = 26 - p;  // c_q = -c_p, first nonzero component +1
+        const V cu = dot(qcx(q), qcy(q), qcz(q), ux, uy, uz);
+        const V cF = dot(qcx(q), qcy(q), qcz(q), Fx, Fy, Fz);
+        const V pe = smul(vc<V>(wq(q)), sfma(cu, sfma(k1, cu, smul(s9, cF)), k0));
+        const V po = smul(vc<V>(3.0f * wq(q)), sfma(om_rho, cu, smul(src, cF)));
+        h[q] = sfma(a, h[q], sadd(pe, po));
+        h[p] = sfma(a, h[p], ssub(pe, po));
     }
-    h[13] = fmaf(a, h[13], wq(13) * k0);
+    h[13] = sfma(a, h[13], smul(vc<V>(wq(13)), k0));
     drho_o = M.drho;
-    jx_o = M.jx + Fx;
-    jy_o = M.jy + Fy;
-    jz_o = M.jz + Fz;
+    jx_o = sadd(M.jx, Fx);
+    jy_o = sadd(M.jy, Fy);
+    jz_o = sadd(M.jz, Fz);
+}
+
+// One cell (the form every kernel but the paired bulk kernel uses).
+__device__ __forceinline__ void collide_srt_smag(float h[27], float Fx, float Fy, float Fz, float tau0, float smag_c2,
+                                                 float& drho_o, float& jx_o, float& jy_o, float& jz_o)
+{
+    collide_srt_smag_v<float>(h, Fx, Fy, Fz, tau0, smag_c2, drho_o, jx_o, jy_o, jz_o);
 }
 
 // ------------------------------------------------------------------ streaming
@@ -1490,7 +1543,8 @@ __global__ void __launch_bounds__(256, 4) k_bulk(const StepArgs A, const BulkPar
 // pulled values come from 32-bit words too: c_x = 0 from the pair's own word,
 // c_x = -1 from its own and the right neighbour's, c_x = +1 from the left
 // neighbour's and its own.  The collision runs on f32x2 instructions across the
-// two cells (collide_cumulant_v<float2>), bit for bit the one-cell evaluation,
+// two cells (collide_cumulant_v or collide_srt_smag_v on float2), bit for bit
+// the one-cell evaluation,
 // and each store packs the pair with one conversion.  Half the threads of
 // k_bulk, each with two cells' work and about half the instructions per cell;
 // nx must be even (rows and planes then start on 32-bit words).  The launch's
@@ -1524,8 +1578,8 @@ __device__ __forceinline__ unsigned ld_word(const unsigned* p)
     return v;
 }
 
-template <typename T, bool DIAG, bool SINGLE>
-__global__ void __launch_bounds__(128, 4) k_bulk2(const StepArgs A, const BulkParams P)
+template <int COLL, typename T, bool DIAG, bool SINGLE>
+__global__ void __launch_bounds__(128, COLL == COLL_CUMULANT ? 4 : 5) k_bulk2(const StepArgs A, const BulkParams P)
 {
     static_assert(sizeof(T) == 2, "paired cells are for 16-bit storage");
     using W = Pack16<T>;
@@ -1603,7 +1657,11 @@ __global__ void __launch_bounds__(128, 4) k_bulk2(const StepArgs A, const BulkPa
             write_inlet_ghost(D, step + 1, y, z);
         }
         float2 m, jx, jy, jz;
-        collide_cumulant_v<float2>(h, bc2(L.body[0]), bc2(L.body[1]), bc2(L.body[2]), L.omega, m, jx, jy, jz);
+        if (COLL == COLL_CUMULANT)
+            collide_cumulant_v<float2>(h, bc2(L.body[0]), bc2(L.body[1]), bc2(L.body[2]), L.omega, m, jx, jy, jz);
+        else
+            collide_srt_smag_v<float2>(h, bc2(L.body[0]), bc2(L.body[1]), bc2(L.body[2]), L.tau0, L.smag_c2, m, jx,
+                                       jy, jz);
         if (DIAG) {
             o_m = (double)m.x + (double)m.y;
             o_jx = (double)jx.x + (double)jx.y;
@@ -2488,14 +2546,14 @@ static cudaError_t launch_dependent_bulk(void (*kernel)(StepArgs, BulkParams), d
     return cudaLaunchKernelEx(&cfg, kernel, a, p);
 }
 
-// The paired bulk kernel for a collision and storage (the cumulant collision
-// with 16-bit storage); false where it is not built.
+// The paired bulk kernel for a collision and storage (16-bit storage); false
+// where it is not built.
 template <int C, typename T>
 static bool paired_form(void (*&kb)(StepArgs, BulkParams), bool diag, bool single)
 {
-    if constexpr (C == COLL_CUMULANT && sizeof(T) == 2) {
-        kb = diag ? (single ? k_bulk2<T, true, true> : k_bulk2<T, true, false>)
-                  : (single ? k_bulk2<T, false, true> : k_bulk2<T, false, false>);
+    if constexpr (sizeof(T) == 2) {
+        kb = diag ? (single ? k_bulk2<C, T, true, true> : k_bulk2<C, T, true, false>)
+                  : (single ? k_bulk2<C, T, false, true> : k_bulk2<C, T, false, false>);
         return true;
     } else {
         (void)kb;

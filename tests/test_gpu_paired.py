@@ -1,9 +1,9 @@
 """The paired form of the bulk kernel against the one-cell form.
 
-With 16-bit storage and the cumulant collision, the bulk tiles (no cell on a
-no-slip or free-slip face) take two cells of a row per thread: 32-bit loads and
-stores of bf16x2/f16x2 words and the collision on f32x2 instructions across the
-pair.  Every operation rounds as the one-cell evaluation does, so PDFs, rotor
+With 16-bit storage the bulk tiles (no cell on a no-slip or free-slip face)
+take two cells of a row per thread: 32-bit loads and stores of bf16x2/f16x2
+words and the collision (cumulant or BGK-Smagorinsky) on f32x2 instructions
+across the pair.  Every operation rounds as the one-cell evaluation does, so PDFs, rotor
 loads and element forces must agree bit for bit with the one-cell kernel
 (``staged`` 2), on periodic and inlet/outlet lattices, ragged and degenerate
 sizes (nx = 2: one pair on both x faces), several tile shapes, diagnostic steps
@@ -58,25 +58,28 @@ def _same(a, b):
     assert a["diag"][1] == b["diag"][1]
 
 
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
 @pytest.mark.parametrize("storage", ["bf16", "fp16"])
 @pytest.mark.parametrize("shape,tile", [((64, 12, 6), (32, 4)), ((70, 5, 3), (32, 4)), ((2, 3, 4), (32, 4)),
                                         ((130, 6, 5), (64, 2)), ((96, 4, 4), (128, 1)), ((66, 9, 3), (32, 8))])
-def test_paired_bulk_matches_one_cell_periodic(storage, shape, tile):
+def test_paired_bulk_matches_one_cell_periodic(coll, storage, shape, tile):
     nx, ny, nz = shape
-    dom = dict(nx=nx, ny=ny, nz=nz, nu=0.02, body_force=(2e-6, -1e-6, 5e-7))
+    dom = dict(nx=nx, ny=ny, nz=nz, nu=0.02, body_force=(2e-6, -1e-6, 5e-7), collision=coll, smag_c=0.17)
     state = I.random_state(nx, ny, nz, seed=11)
     a = _run(dom, storage, tile, 0, 9, state=state, diag_every=4)
     b = _run(dom, storage, tile, 2, 9, state=state, diag_every=4)
     _same(a, b)
 
 
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
 @pytest.mark.parametrize("storage", ["bf16", "fp16"])
 @pytest.mark.parametrize("tile", [(32, 4), (64, 1)])
-def test_paired_bulk_matches_one_cell_with_inlet_outlet_and_rotor(storage, tile):
+def test_paired_bulk_matches_one_cell_with_inlet_outlet_and_rotor(coll, storage, tile):
     """The rotor case: inlet ghost columns at x = 0 (the first cell of the first
     pair), the outlet's clamped source at x = nx - 1 (the second cell of the last
     pair), inflow noise, and a rotor whose sampling reads the pairs' stores."""
     dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777)
+    dom["collision"] = coll
     a = _run(dom, storage, tile, 0, 12, turb=turb, inflow=True, diag_every=5)
     b = _run(dom, storage, tile, 2, 12, turb=turb, inflow=True, diag_every=5)
     _same(a, b)
