@@ -150,16 +150,6 @@ __device__ __forceinline__ void feq_offsets(float drho, float ux, float uy, floa
     }
 }
 
-__device__ __forceinline__ float feq_offset_one(int q, float ux, float uy, float uz)
-{
-    float px[3], dx[3], py[3], dy[3], pz[3], dz[3];
-    axis_factors(ux, px, dx);
-    axis_factors(uy, py, dy);
-    axis_factors(uz, pz, dz);
-    const int i = q % 3, j = (q / 3) % 3, k = q / 9;
-    return dx[i] * py[j] * pz[k] + w1(i - 1) * (dy[j] * pz[k] + w1(j - 1) * dz[k]);
-}
-
 // Inlet ghost populations of column (y, z) for step `step`: the offsets
 // feq_q(rho = 1, u_in) - w_q of the nine directions with c_x = +1 (the values
 // the x = 0 cells pull across the inlet face from that column), written once
@@ -170,10 +160,17 @@ __device__ __forceinline__ void write_inlet_ghost(const DevDomain* D, long long 
     inflow_velocity(D, step, y, z, u);
     float* g = D->inflow_ghost[step & 1];
     const int plane = D->ny * D->nz, col = z * D->ny + y;
+    // feq_q(1, u) - w_q = dphi_x phi_y phi_z + w1(c_x) (dphi_y phi_z + w1(c_y) dphi_z) for the
+    // nine directions with c_x = +1, the axis factors formed once
+    float px[3], dx[3], py[3], dy[3], pz[3], dz[3];
+    axis_factors(u[0], px, dx);
+    axis_factors(u[1], py, dy);
+    axis_factors(u[2], pz, dz);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) g[(k * 3 + j) * plane + col] = feq_offset_one(k * 9 + j * 3 + 2, u[0], u[1], u[2]);
+        for (int j = 0; j < 3; ++j)
+            g[(k * 3 + j) * plane + col] = dx[2] * py[j] * pz[k] + w1(1) * (dy[j] * pz[k] + w1(j - 1) * dz[k]);
 }
 
 // ------------------------------------------------------------------ moments
