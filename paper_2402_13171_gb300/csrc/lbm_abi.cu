@@ -438,6 +438,29 @@ AlmArgs alm_args(Batch* b, const long long* step_slot, int slot, long long step,
     return a;
 }
 
+// Per-lattice values the bulk kernels take as kernel parameters (constant bank)
+// instead of loading them from the device descriptors.
+static BulkParams bulk_params(const Batch* b)
+{
+    BulkParams bp{};
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        const DevDomain& h = b->inst[i].h;
+        LatHot& L = bp.lat[i];
+        L.nx = h.nx;
+        L.ny = h.ny;
+        L.nz = h.nz;
+        L.N = (unsigned)h.N;
+        L.inout = h.bc[0] == BC_INOUT ? 1 : 0;
+        L.omega = h.omega;
+        L.tau0 = h.tau0;
+        L.smag_c2 = h.smag_c2;
+        for (int a3 = 0; a3 < 3; ++a3) L.body[a3] = h.body[a3];
+        L.f[0] = h.f[0];
+        L.f[1] = h.f[1];
+    }
+    return bp;
+}
+
 // One time step.  Staged rows: one persistent launch over the whole work list,
 // then (with rotors) the actuator line of the next step.  Otherwise (k_step or,
 // in place, k_step_aa) the rotor tiles (first in the list), the actuator line
@@ -469,7 +492,22 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
             // after an even step the pulled populations of a cell are its own opposite slots
             CK(launch_alm(b->store, alm_args(b, b->d_step, parity, 0, 0, parity == 1 ? 0 : 1), b->stream, true));
         }
-        if (Nb > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nb), block, b->stream, ab, parity == 1, false, R > 0));
+        if (!(b->pairs_ok && !b->single_cell)) {
+            if (Nb > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nb), block, b->stream, ab, parity == 1, false, R > 0));
+            return LBM_OK;
+        }
+        // 16-bit storage: the tiles with a wall-face cell one cell per thread, the
+        // rest two cells per thread
+        StepArgs af = ab, ap = ab;
+        af.n_tiles = Nf;
+        af.write_step = Np == 0 ? 1 : 0;
+        ap.tiles = b->d_tiles + R + Nf;
+        ap.n_tiles = Np;
+        if (Nf > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nf), block, b->stream, af, parity == 1, false, R > 0));
+        if (Np > 0) {
+            const BulkParams bp = bulk_params(b);
+            CK(launch_step_aa(b->coll, b->store, dim3(Np), block, b->stream, ap, parity == 1, false, R + Nf > 0, &bp));
+        }
         return LBM_OK;
     }
     // rotor tiles and the actuator line, then the face tiles (the general
@@ -491,22 +529,7 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
     }
     if (Nf > 0) CK(launch_step(b->coll, b->store, dim3(Nf), block, b->stream, af, false, R > 0));
     if (Np > 0) {
-        BulkParams bp{};
-        for (size_t i = 0; i < b->inst.size(); ++i) {
-            const DevDomain& h = b->inst[i].h;
-            LatHot& L = bp.lat[i];
-            L.nx = h.nx;
-            L.ny = h.ny;
-            L.nz = h.nz;
-            L.N = (unsigned)h.N;
-            L.inout = h.bc[0] == BC_INOUT ? 1 : 0;
-            L.omega = h.omega;
-            L.tau0 = h.tau0;
-            L.smag_c2 = h.smag_c2;
-            for (int a3 = 0; a3 < 3; ++a3) L.body[a3] = h.body[a3];
-            L.f[0] = h.f[0];
-            L.f[1] = h.f[1];
-        }
+        const BulkParams bp = bulk_params(b);
         const bool tiled = b->tile_z == 1;  // k_bulk takes single-plane tiles
         const bool pairs = tiled && b->pairs_ok && !b->single_cell;
         CK(launch_step(b->coll, b->store, dim3(Np), block, b->stream, ap, false, R + Nf > 0, tiled ? &bp : nullptr,
@@ -1543,7 +1566,8 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
     // the same split as launch_one
     // (with rotors: the rotor tiles and the actuator line)
     if (b->staged) *launches = 1 + (b->n_rotor > 0 ? 1 : 0);
-    else if (b->inplace) *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
+    else if (b->inplace && !(b->pairs_ok && !b->single_cell))
+        *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
     else
         *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_face > 0 ? 1 : 0) +
                     (b->n_tiles > b->n_rotor + b->n_face ? 1 : 0);

@@ -203,9 +203,11 @@ cudaError_t launch_step(int coll, int store, dim3 grid, dim3 block, cudaStream_t
                         bool dependent, const BulkParams* bulk = nullptr, bool diag_step = false, bool pairs = false);
 // The in-place (AA) step over the whole work list: odd steps read and write a
 // cell's own slots, even steps pull and push across neighbours.
-// rotor / dependent as for launch_step.
+// rotor / dependent as for launch_step; pairs (the lattices' per-cell
+// parameters, or nullptr): tiles without a wall-face cell, two cells of a row
+// per thread (16-bit storage, every nx even).
 cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd,
-                           bool rotor, bool dependent);
+                           bool rotor, bool dependent, const BulkParams* pairs = nullptr);
 // Outlet copies of an in-place lattice for step `step`, from its current state.
 cudaError_t launch_outlet_fill(int store, const DevDomain* d_dom_inst, const DevDomain& h, long long step,
                                cudaStream_t s);

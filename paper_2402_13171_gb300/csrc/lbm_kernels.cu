@@ -1975,6 +1975,185 @@ __global__ void __launch_bounds__(256, ROTOR ? 2 : (COLL == COLL_CUMULANT ? 4 : 
 
 // Outlet copies of the last plane for step `step` from the array's current
 // (pull-scheme) state, after a state change of an in-place lattice.
+// The in-place step over the tiles without a no-slip or free-slip face cell,
+// two cells of a row per thread (16-bit storage, nx even), as k_bulk2 does for
+// the pull scheme.  Odd steps read a cell's own opposite slots and write its own
+// slots: for the pair (x, x + 1) one 32-bit word per plane each way.  Even steps
+// pull from the neighbours' words like k_bulk2 and store f*_q into the slot read
+// for the opposite direction: with no x shift that is one word of the pair's
+// own; shifted by one cell it straddles two words, and the two cells store their
+// halves with 16-bit stores.  Every slot a thread writes is one it read itself;
+// a neighbour may rewrite the other half of a word this thread loaded, a half it
+// does not use.  Inlet and outlet as in aa_cell.  Bit for bit the one-cell form.
+__device__ __forceinline__ void st_half(void* p, unsigned short v)
+{
+    asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"(v) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ unsigned short to_bits16(float v);
+template <>
+__device__ __forceinline__ unsigned short to_bits16<__nv_bfloat16>(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <>
+__device__ __forceinline__ unsigned short to_bits16<__half>(float v)
+{
+    return __half_as_ushort(__float2half_rn(v));
+}
+
+template <int COLL, typename T, bool ODD, bool SINGLE>
+__global__ void __launch_bounds__(128, SINGLE ? 5 : 4) k_step_aa2(const StepArgs A, const BulkParams P)
+{
+    static_assert(sizeof(T) == 2, "paired cells are for 16-bit storage");
+    using W = Pack16<T>;
+    __shared__ double s_red[8][4];
+    const unsigned long long tile = ld_tile(A.tiles + blockIdx.x);
+    const int inst = SINGLE ? 0 : tile_lattice(tile);
+    const LatHot& L = P.lat[inst];
+    const int z = (int)((tile >> 32) & 0xFFFF);
+    const int y = (int)((tile >> 16) & 0xFFFF) + threadIdx.y;
+    const int x0 = (int)(tile & 0xFFFF);
+    const int x = x0 + 2 * (int)threadIdx.x;  // cells x, x + 1
+    const DevDomain* D = A.dom + inst;  // the inlet and outlet buffers only
+    const long long step = __ldcg(A.step_slot + A.parity);
+    if (A.write_step && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        A.step_slot[A.parity ^ 1] = step + 1;
+        A.diag_flag[A.parity ^ 1] = A.diag_every > 0 && (step + 1) % A.diag_every == 0;
+    }
+    const bool diag = __ldcg(A.diag_flag + A.parity) != 0;
+    double o_m = 0.0, o_jx = 0.0, o_jy = 0.0, o_jz = 0.0;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    if (x < nx && y < ny) {
+        unsigned* fw = (unsigned*)L.f[0];
+        const unsigned N2 = L.N >> 1;  // words per plane
+        const bool inout = L.inout != 0;
+        int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+        if (ym < 0) ym += ny; if (yp >= ny) yp -= ny;
+        if (zm < 0) zm += nz; if (zp >= nz) zp -= nz;
+        const unsigned ys[3] = {(unsigned)yp, (unsigned)y, (unsigned)ym};
+        const unsigned zs[3] = {(unsigned)zp, (unsigned)z, (unsigned)zm};
+        const unsigned nx2 = (unsigned)nx >> 1, nxy2 = nx2 * (unsigned)ny;
+        const unsigned xw = (unsigned)x >> 1;
+        const bool at_in = inout && x == 0, at_out = inout && x + 2 == nx;
+        // left and right neighbour words relative to the pair's own: wrapped on a
+        // periodic x, else the own word (the inlet and outlet replace those values)
+        int dl = -1, dr = 1;
+        if (x == 0) dl = inout ? 0 : (int)nx2 - 1;
+        if (x + 2 == nx) dr = inout ? 0 : -((int)nx2 - 1);
+        float2 h[27];
+        if (ODD) {
+            const unsigned* own = fw + (((unsigned)z * (unsigned)ny + (unsigned)y) * nx2 + xw);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const unsigned w = own[(size_t)(26 - q) * N2];
+                h[q] = make_float2(W::lo(w), W::hi(w));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const unsigned* zr = fw + zs[k] * nxy2;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const unsigned* r = zr + (ys[j] * nx2 + xw);
+                    const int q = k * 9 + j * 3;
+                    const unsigned* p0 = r + (size_t)q * N2;         // c_x = -1: sources x + 1, x + 2
+                    const unsigned* p1 = r + (size_t)(q + 1) * N2;   // c_x = 0
+                    const unsigned* p2 = r + (size_t)(q + 2) * N2;   // c_x = +1: sources x - 1, x
+                    const unsigned o0 = *p0, r0 = p0[dr];
+                    const unsigned o1 = *p1;
+                    const unsigned l2 = p2[dl], o2 = *p2;
+                    h[q] = make_float2(W::hi(o0), W::lo(r0));
+                    h[q + 1] = make_float2(W::lo(o1), W::hi(o1));
+                    h[q + 2] = make_float2(W::hi(l2), W::lo(o2));
+                }
+            }
+        }
+        const int plane = ny * nz;
+        if (at_in) {
+            // the x = 0 cell across the inlet: ghosts of the columns (y - c_y, z - c_z)
+            const float* gb = D->inflow_ghost[step & 1];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    h[k * 9 + j * 3 + 2].x = gb[(k * 3 + j) * plane + (int)zs[k] * ny + (int)ys[j]];
+        }
+        if (at_out) {
+            // the x = nx - 1 cell across the outlet: the last plane's copies there
+            const float* ob = D->outlet[step & 1];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    h[k * 9 + j * 3].y = ob[(k * 3 + j) * plane + (int)zs[k] * ny + (int)ys[j]];
+        }
+        if (at_in) write_inlet_ghost(D, step + 1, y, z);
+        float2 m, jx, jy, jz;
+        if (COLL == COLL_CUMULANT)
+            collide_cumulant_v<float2>(h, bc2(L.body[0]), bc2(L.body[1]), bc2(L.body[2]), L.omega, m, jx, jy, jz);
+        else
+            collide_srt_smag_v<float2>(h, bc2(L.body[0]), bc2(L.body[1]), bc2(L.body[2]), L.tau0, L.smag_c2, m, jx,
+                                       jy, jz);
+        if (diag) {
+            o_m = (double)m.x + (double)m.y;
+            o_jx = (double)jx.x + (double)jx.y;
+            o_jy = (double)jy.x + (double)jy.y;
+            o_jz = (double)jz.x + (double)jz.y;
+        }
+        if (at_out) {
+            // the outlet copy for step n+1: f*_q of the last plane, directions with
+            // c_x = -1, as the array would hold it (rounded to the storage type)
+            float* ob = D->outlet[(step + 1) & 1];
+            const int col = z * ny + y;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) ob[(k * 3 + j) * plane + col] = Io<T>::round(h[k * 9 + j * 3].y);
+        }
+        // the store slots are the load slots, recomputed from opaque copies of the
+        // coordinates: kept live across the collision they would spill
+        unsigned long long fa = (unsigned long long)fw;
+        int xo = x, yo = y, zo = z;
+        asm volatile("" : "+l"(fa), "+r"(xo), "+r"(yo), "+r"(zo));
+        unsigned* fs = (unsigned*)fa;
+        const unsigned xwo = (unsigned)xo >> 1;
+        if (ODD) {
+            unsigned* own = fs + (((unsigned)zo * (unsigned)ny + (unsigned)yo) * nx2 + xwo);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) own[(size_t)q * N2] = W::pack(h[q].x, h[q].y);
+        } else {
+            int ymo = yo - 1, ypo = yo + 1, zmo = zo - 1, zpo = zo + 1;
+            if (ymo < 0) ymo += ny; if (ypo >= ny) ypo -= ny;
+            if (zmo < 0) zmo += nz; if (zpo >= nz) zpo -= nz;
+            const unsigned yso[3] = {(unsigned)ypo, (unsigned)yo, (unsigned)ymo};
+            const unsigned zso[3] = {(unsigned)zpo, (unsigned)zo, (unsigned)zmo};
+            const bool in_o = inout && xo == 0, out_o = inout && xo + 2 == nx;
+            int dlo = -1, dro = 1;
+            if (xo == 0) dlo = inout ? 0 : (int)nx2 - 1;
+            if (xo + 2 == nx) dro = inout ? 0 : -((int)nx2 - 1);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                // f*_q goes to the slot read for the opposite direction p, in plane p
+                // at the cells x + c_q, unless it leaves through the inlet or the outlet
+                const int p = 26 - q;
+                unsigned* w = fs + (size_t)p * N2 + zso[p / 9] * nxy2 + yso[(p / 3) % 3] * nx2 + xwo;
+                if (qcx(q) == 0) {
+                    *w = W::pack(h[q].x, h[q].y);
+                } else if (qcx(q) == 1) {  // cells x + 1 (high half of the own word) and x + 2
+                    *((unsigned short*)w + 1) = to_bits16<T>(h[q].x);
+                    if (!out_o) *(unsigned short*)(w + dro) = to_bits16<T>(h[q].y);
+                } else {                   // cells x - 1 (high half of the left word) and x
+                    if (!in_o) *((unsigned short*)(w + dlo) + 1) = to_bits16<T>(h[q].x);
+                    *(unsigned short*)w = to_bits16<T>(h[q].y);
+                }
+            }
+        }
+    }
+    if (diag) diag_close(A, D, step, o_m, o_jx, o_jy, o_jz, s_red);
+    if (blockIdx.x == gridDim.x - 1) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <typename T>
 __global__ void k_outlet_fill(const DevDomain* D, long long step)
 {
@@ -2494,11 +2673,29 @@ static cudaError_t launch_dependent(void (*kernel)(StepArgs), dim3 grid, dim3 bl
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+// The paired in-place kernel for a collision, storage and step parity
+// (16-bit storage); nullptr where it is not built.
+static cudaError_t launch_dependent_bulk(void (*kernel)(StepArgs, BulkParams), dim3 grid, dim3 block, cudaStream_t s,
+                                         const StepArgs& a, const BulkParams& p);
+
+template <int C, typename T, bool O>
+static void (*paired_aa(bool single))(StepArgs, BulkParams)
+{
+    if constexpr (sizeof(T) == 2) return single ? k_step_aa2<C, T, O, true> : k_step_aa2<C, T, O, false>;
+    else return nullptr;
+}
+
 cudaError_t launch_step_aa(int coll, int store, dim3 grid, dim3 block, cudaStream_t s, const StepArgs& a, bool odd,
-                           bool rotor, bool dependent)
+                           bool rotor, bool dependent, const BulkParams* pairs)
 {
 #define LBM_AA_ONE(C, T, O)                                                                        \
-    if (rotor) k_step_aa<C, T, O, true><<<grid, block, 0, s>>>(a);                                 \
+    if (pairs && !rotor) {                                                                         \
+        void (*k2)(StepArgs, BulkParams) = paired_aa<C, T, O>(a.n_inst == 1);                      \
+        if (!k2) return cudaErrorInvalidValue;                                                     \
+        const dim3 b2(block.x / 2, block.y);                                                       \
+        if (dependent) return launch_dependent_bulk(k2, grid, b2, s, a, *pairs);                   \
+        k2<<<grid, b2, 0, s>>>(a, *pairs);                                                         \
+    } else if (rotor) k_step_aa<C, T, O, true><<<grid, block, 0, s>>>(a);                          \
     else if (dependent) return launch_dependent(k_step_aa<C, T, O, false>, grid, block, s, a);     \
     else k_step_aa<C, T, O, false><<<grid, block, 0, s>>>(a);
 #define LBM_AA_CASE(C, S, T)                         \

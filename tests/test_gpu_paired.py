@@ -116,3 +116,66 @@ def test_forms_where_pairs_do_not_apply():
         a = _run(dom, storage, (32, 4), 0, 5, state=state)
         b = _run(dom, storage, (32, 4), 2, 5, state=state)
         _same(a, b)
+
+
+def _run_aa(dom, storage, tile, form, steps, state=None, turb=None, inflow=False, diag_every=0):
+    """The in-place scheme (one PDF array) for `steps` steps, an even count."""
+    from paper_2402_13171_gb300 import lbm
+    g = lbm.Lattice.create(dom["nx"], dom["ny"], dom["nz"], collision=dom.get("collision", "cumulant"),
+                           nu=dom.get("nu", 0.02), smag_c=dom.get("smag_c", 0.17), storage=storage,
+                           bc=dom.get("bc", ("periodic",) * 3), body_force=dom.get("body_force", (0, 0, 0)),
+                           seed=dom.get("seed", 0), diag_every=diag_every, tile=tuple(tile) + (1, form), inplace=True)
+    if inflow:
+        g.set_inflow(u_ref=dom["u_ref"], noise_rel=dom.get("noise_rel", 0.0))
+    if turb is not None:
+        g.add_turbine(**turb)
+    if state is not None:
+        g.init_fields(*state)
+    elif not inflow:
+        g.init_fields(None, None, None)
+    out = []
+    for n in steps:   # odd and even steps, graph replays and single launches
+        g.step(n)
+        if g.step_count() % 2 == 0:
+            out.append(g.pdfs())
+    loads = g.loads(0, elements=True) if turb is not None else None
+    g.destroy()
+    return out, loads
+
+
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+@pytest.mark.parametrize("shape,tile,bc", [((64, 12, 6), (32, 4), ("periodic",) * 3),
+                                           ((70, 5, 3), (32, 4), ("periodic",) * 3),
+                                           ((2, 3, 4), (32, 4), ("periodic",) * 3),
+                                           ((130, 6, 5), (64, 2), ("periodic",) * 3),
+                                           ((40, 12, 10), (32, 4), ("periodic", "freeslip", "noslip"))])
+def test_paired_inplace_matches_one_cell(coll, storage, shape, tile, bc):
+    """The in-place scheme's paired form (odd steps on a pair's own words, even
+    steps with half-word stores into the neighbours' words) against its
+    one-cell form, bit for bit after every even step; on a lattice with wall
+    faces the face tiles keep one cell per thread in a launch of their own."""
+    nx, ny, nz = shape
+    dom = dict(nx=nx, ny=ny, nz=nz, nu=0.02, body_force=(2e-6, -1e-6, 5e-7), collision=coll, bc=bc)
+    state = I.random_state(nx, ny, nz, seed=13, u_mean=(0.03, -0.01, 0.02), du=0.01, drho=0.005)
+    a, _ = _run_aa(dom, storage, tile, 0, (1, 1, 2, 8, 3, 1), state=state, diag_every=4)
+    b, _ = _run_aa(dom, storage, tile, 2, (1, 1, 2, 8, 3, 1), state=state, diag_every=4)
+    assert len(a) == len(b) == 4
+    for fa, fb in zip(a, b):
+        np.testing.assert_array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
+def test_paired_inplace_with_inlet_outlet_and_rotor(coll):
+    """In place with the inlet ghosts (the x = 0 cell of the first pair), the
+    outlet copies (the x = nx - 1 cell of the last pair), inflow noise and a
+    rotor whose sampling reads the array in the layout each step leaves."""
+    dom, turb = I.single_turbine_case(64, 40, 40, diameter=16.0, elements_per_blade=8, seed=777)
+    dom["collision"] = coll
+    a, la = _run_aa(dom, "bf16", (32, 4), 0, (1, 1, 2, 8), turb=turb, inflow=True, diag_every=5)
+    b, lb = _run_aa(dom, "bf16", (32, 4), 2, (1, 1, 2, 8), turb=turb, inflow=True, diag_every=5)
+    for fa, fb in zip(a, b):
+        np.testing.assert_array_equal(fa, fb)
+    assert la[:2] == lb[:2]
+    np.testing.assert_array_equal(la[2], lb[2])
+    np.testing.assert_array_equal(la[3], lb[3])
