@@ -438,6 +438,14 @@ AlmArgs alm_args(Batch* b, const long long* step_slot, int slot, long long step,
     return a;
 }
 
+// Two cells of a row per thread: 16-bit storage, every nx even, not the
+// one-cell form, and CTAs of whole warps (tile_x * tile_y / 2 threads a
+// multiple of 32, for the warp-wide reductions).
+static bool pair_tiles(const Batch* b)
+{
+    return b->pairs_ok && !b->single_cell && (b->tile_x * b->tile_y) % 64 == 0;
+}
+
 // Per-lattice values the bulk kernels take as kernel parameters (constant bank)
 // instead of loading them from the device descriptors.
 static BulkParams bulk_params(const Batch* b)
@@ -492,7 +500,7 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
             // after an even step the pulled populations of a cell are its own opposite slots
             CK(launch_alm(b->store, alm_args(b, b->d_step, parity, 0, 0, parity == 1 ? 0 : 1), b->stream, true));
         }
-        if (!(b->pairs_ok && !b->single_cell)) {
+        if (!pair_tiles(b)) {
             if (Nb > 0) CK(launch_step_aa(b->coll, b->store, dim3(Nb), block, b->stream, ab, parity == 1, false, R > 0));
             return LBM_OK;
         }
@@ -531,7 +539,7 @@ lbm_status launch_one(Batch* b, int parity, bool diag_step = false)
     if (Np > 0) {
         const BulkParams bp = bulk_params(b);
         const bool tiled = b->tile_z == 1;  // k_bulk takes single-plane tiles
-        const bool pairs = tiled && b->pairs_ok && !b->single_cell;
+        const bool pairs = tiled && pair_tiles(b);
         CK(launch_step(b->coll, b->store, dim3(Np), block, b->stream, ap, false, R + Nf > 0, tiled ? &bp : nullptr,
                        diag_step, pairs));
     }
@@ -1566,7 +1574,7 @@ lbm_status lbm_get_launches_per_step(lbm_ctx* ctx, int* launches)
     // the same split as launch_one
     // (with rotors: the rotor tiles and the actuator line)
     if (b->staged) *launches = 1 + (b->n_rotor > 0 ? 1 : 0);
-    else if (b->inplace && !(b->pairs_ok && !b->single_cell))
+    else if (b->inplace && !pair_tiles(b))
         *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_tiles > b->n_rotor ? 1 : 0);
     else
         *launches = (b->n_rotor > 0 ? 2 : 0) + (b->n_face > 0 ? 1 : 0) +

@@ -906,23 +906,50 @@ __device__ __forceinline__ float tip_loss_factor(int n_blades, float R, float r,
     return 0.63661977f * acosf(expf(-f));  // 2/pi
 }
 
+// Normaliser of an element's spreading kernel at position p: the product over
+// the axes of the sums of the kernel's weights over the lattice points within
+// the cut (exp(-(i - p)^2 / eps^2) for the Gaussian; 1 up to rounding for Roma).
+__device__ __forceinline__ float spread_norm(const DevTurbine* B, const float p[3])
+{
+    float S = 1.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lo = (int)ceilf(p[a] - B->cut), hi = (int)floorf(p[a] + B->cut);
+        float sa = 0.0f;
+        if (B->roma) {
+            for (int j = lo; j <= hi; ++j) sa += roma_phi((float)j - p[a]);
+        } else {
+            for (int j = lo; j <= hi; ++j) {
+                const float d = (float)j - p[a];
+                sa += expf(-d * d * B->inv_eps2);
+            }
+        }
+        S *= sa;
+    }
+    return S;
+}
+
 // Actuator line of step `step` for the blade elements [e0, e0 + kAlmBlock) of
 // one lattice, by the whole CTA.  Reads the populations of the current array f
 // (post-collision of step-1) and the box force of step-1; writes the element
 // positions with their spreading normalisation, blade forces and FP64 load
 // parts of those elements into the buffers of parity step & 1.
-//  phase 0, one thread per element: blade kinematics (Algorithm 2);
+//  phase 0, one thread per element: blade kinematics (Algorithm 2) and the
+//    kernel normaliser, which depend on the step alone;
+//  then, in a dependent launch, the wait for the launch before it (the rotor
+//    tiles, which write the cells sampled below and the box force);
 //  phase 1, one thread per (element, corner): pull the 27 populations of the
 //    corner cell, rho and u = (sum c f + F/2)/rho at the corner;
 //  phase 2, one thread per element: trilinear blend, relative velocity,
 //    angle of attack, polars, blade force (with the tip-loss factor if set),
-//    kernel normalisation, FP64 load parts.
+//    FP64 load parts.
 // Each element's values depend on that element alone, so blocks of elements
 // may run in separate CTAs.
 template <typename T>
 __device__ __noinline__ void alm_block(const DevDomain* D, const T* f, long long step, int swapped, int e0)
 {
     __shared__ ElementGeo s_geo[kAlmBlock];
+    __shared__ float s_norm[kAlmBlock];
     __shared__ float4 s_corner[8 * kAlmBlock];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
@@ -930,8 +957,13 @@ __device__ __noinline__ void alm_block(const DevDomain* D, const T* f, long long
     const long long N = D->N;
     const int n[3] = {D->nx, D->ny, D->nz};
     const int ne = min(kAlmBlock, D->n_el - e0);
-    for (int i = tid; i < ne; i += nthr) element_geometry(D, e0 + i, step, s_geo[i]);
+    for (int i = tid; i < ne; i += nthr) {
+        element_geometry(D, e0 + i, step, s_geo[i]);
+        s_norm[i] = spread_norm(s_geo[i].B, s_geo[i].p);
+    }
     __syncthreads();
+    // a no-op outside a dependent launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int pc = tid; pc < 8 * ne; pc += nthr) {
         const int i = pc >> 3, cn = pc & 7;
         int c[3];
@@ -1018,23 +1050,7 @@ __device__ __noinline__ void alm_block(const DevDomain* D, const T* f, long long
 #pragma unroll
             for (int a = 0; a < 3; ++a) Fb[a] = sc * (CL * eL[a] + CD * eD[a]);
         }
-        // normalisation: per-axis sums of the kernel's weights over |i - p| <= cut
-        // (exp(-(i - p)^2 / eps^2) for the Gaussian; 1 up to rounding for Roma)
-        float S = 1.0f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int lo = (int)ceilf(G.p[a] - B->cut), hi = (int)floorf(G.p[a] + B->cut);
-            float sa = 0.0f;
-            if (B->roma) {
-                for (int j = lo; j <= hi; ++j) sa += roma_phi((float)j - G.p[a]);
-            } else {
-                for (int j = lo; j <= hi; ++j) {
-                    const float d = (float)j - G.p[a];
-                    sa += expf(-d * d * B->inv_eps2);
-                }
-            }
-            S *= sa;
-        }
+        const float S = s_norm[i];
         D->el_pos[par][g] = make_float4(G.p[0], G.p[1], G.p[2], 1.0f / S);
         D->el_force[par][g] = make_float4(Fb[0], Fb[1], Fb[2], alpha);
         D->el_load[2 * g] = (double)Fb[0] * ea[0] + (double)Fb[1] * ea[1] + (double)Fb[2] * ea[2];
@@ -2509,13 +2525,15 @@ __global__ void __launch_bounds__(256, 3) k_step_staged(const StepArgs A)
 // The actuator line as its own launch: CTA b of a lattice evaluates its
 // elements [32 b, 32 b + 32), and the last of the lattice's CTAs to finish adds
 // up the per-rotor loads.  In a time step it follows the rotor launch: it lets
-// the step's next launch start at once, then waits on the device until the
-// rotor tiles (which write the cells it samples and the box force) are done.
+// the step's next launch start at once, forms the blade geometry and kernel
+// normalisers, then waits on the device until the rotor tiles (which write the
+// cells it samples and the box force) are done.  What it reads before that
+// wait (the step counter, the turbines' parameters) was written before the
+// rotor launch, which starts only after the previous step has completed.
 template <typename T>
 __global__ void __launch_bounds__(256) k_alm(const AlmArgs A)
 {
     asm volatile("griddepcontrol.launch_dependents;");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ int s_last;
     int inst = 0;
     while (inst + 1 < A.n_inst && A.cta_off[inst + 1] <= (int)blockIdx.x) ++inst;

@@ -203,3 +203,34 @@ def test_paired_inplace_batch_matches_one_cell():
         np.testing.assert_array_equal(L.pdfs(), ref[-1])
     for L in lat:
         L.destroy()
+
+
+@pytest.mark.parametrize("coll", ["cumulant", "srt_smag"])
+def test_paired_bulk_beside_a_rotor_at_a_wall_face(coll):
+    """A rotor whose force box comes within a tile of a free-slip face: rotor
+    tiles on the face, face tiles (one cell per thread) and the paired bulk in
+    one step, bit for bit the one-cell form's results."""
+    dom, turb = I.single_turbine_case(64, 34, 40, diameter=16.0, elements_per_blade=8, seed=779)
+    dom["collision"] = coll
+    dom["bc"] = ("inout", "freeslip", "periodic")
+    a = _run(dom, "bf16", (32, 4), 0, 12, turb=turb, inflow=True, diag_every=5)
+    b = _run(dom, "bf16", (32, 4), 2, 12, turb=turb, inflow=True, diag_every=5)
+    _same(a, b)
+
+
+def test_tiles_of_partial_warps_keep_one_cell():
+    """Tiles of 32 x 1 and 32 x 3 cells would give paired CTAs of 16 and 48
+    threads, not whole warps: the two-array and in-place steps then run one cell
+    per thread, with diagnostics, and agree with the one-cell form."""
+    dom = dict(nx=64, ny=9, nz=4, nu=0.02, body_force=(2e-6, 0.0, 0.0))
+    state = I.random_state(64, 9, 4, seed=5)
+    for tile in ((32, 1), (32, 3)):
+        a = _run(dom, "bf16", tile, 0, 5, state=state, diag_every=2)
+        b = _run(dom, "bf16", tile, 2, 5, state=state, diag_every=2)
+        np.testing.assert_array_equal(a["pdfs"], b["pdfs"])
+        np.testing.assert_array_equal(a["diag"][0], b["diag"][0])
+        assert a["diag"][1] == b["diag"][1]
+        c, _ = _run_aa(dom, "bf16", tile, 0, (2, 2), state=state, diag_every=2)
+        d, _ = _run_aa(dom, "bf16", tile, 2, (2, 2), state=state, diag_every=2)
+        for u, v in zip(c, d):
+            np.testing.assert_array_equal(u, v)
