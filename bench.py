@@ -114,10 +114,18 @@ NCU_TRAFFIC = {
         ("single_turbine_256x128x128", "fp32", "cumulant", "32x8x1"): 464846080 + 386084096,
         ("single_turbine_256x128x128", "fp32", "cumulant", "64x1x1"): 460046080 + 370189056,
         ("single_turbine_256x128x128", "fp32", "cumulant", "64x2x1"): 459883264 + 369536000,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "32x2x1"): 465237760 + 385448704,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "64x4x1"): 459782912 + 369896704,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "128x1x1"): 459787520 + 369744640,
+        ("single_turbine_256x128x128", "fp32", "cumulant", "128x2x1"): 459758080 + 369656320,
         ("single_turbine_256x128x128", "bf16", "cumulant", "32x4x1"): 243667968 + 176583168,
         ("single_turbine_256x128x128", "bf16", "cumulant", "32x8x1"): 243569920 + 176768512,
         ("single_turbine_256x128x128", "bf16", "cumulant", "64x1x1"): 236081152 + 163854848,
         ("single_turbine_256x128x128", "bf16", "cumulant", "64x2x1"): 236033536 + 163473408,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "32x2x1"): 243940864 + 176277248,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "64x4x1"): 235862016 + 163803904,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "128x1x1"): 235836416 + 163271168,
+        ("single_turbine_256x128x128", "bf16", "cumulant", "128x2x1"): 235859456 + 162748160,
         ("periodic_256x128x128_inplace", "bf16", "cumulant", "32x8x1"): 226669440 + 169525376,
     },
 }
